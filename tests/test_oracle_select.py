@@ -1,0 +1,140 @@
+"""Pins of the portability-tuning oracle (selection arithmetic)."""
+
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import select as osel
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def test_hand_worked_tiny_table():
+    g = _load("select_tiny.json")
+    t = np.array(g["times"])
+    assert list(osel.per_shape_best(t)) == g["t_best"]
+    for k, opt in g["optimum"].items():
+        kappa, val = osel.portability_tune_exhaustive(t, int(k), range(t.shape[1]))
+        assert kappa == opt["kappa"], k
+        assert val == pytest.approx(opt["value"], rel=1e-12)
+
+
+def test_table5_post_processing_arithmetic():
+    g = _load("table5_quadro.json")
+    slow, best = g["rows"]
+    t_best = best["runtime_ms"]
+    assert round(osel.slowdown_vs_best(best["runtime_ms"], t_best), 2) == best["slowdown_vs_oracle"]
+    assert round(osel.slowdown_vs_best(slow["runtime_ms"], t_best), 2) == slow["slowdown_vs_oracle"]
+    # Worst time implied by the best row, then the slow row's speedup from it.
+    t_worst = t_best * best["speedup_vs_worst"]
+    assert round(osel.speedup_vs_worst(slow["runtime_ms"], t_worst), 2) == slow["speedup_vs_worst"]
+    # The two rows imply the same worst time to within print rounding.
+    assert abs(slow["runtime_ms"] * slow["speedup_vs_worst"] - t_worst) / t_worst < 1e-3
+
+
+def test_post_processing_on_a_table():
+    t = np.array([[2.0, 9.0], [4.0, 3.0], [np.inf, 6.0]])
+    assert list(osel.per_shape_best(t)) == [2.0, 3.0]
+    assert list(osel.per_shape_worst(t)) == [4.0, 9.0]
+    assert osel.autotune(t, 0) == 0 and osel.autotune(t, 1) == 1
+
+
+def test_search_space_count_section_iv_c():
+    # 1,343 Quadro variants, best 3, 10 inputs: "over 24 billion" evaluations.
+    n = osel.search_space_evaluations(10, 1343, 3)
+    assert n == 10 * 1343 ** 3
+    assert 24e9 < n < 25e9
+
+
+def _random_table(seed, V, S, invalid=0.1):
+    rng = np.random.default_rng(seed)
+    t = np.exp(rng.normal(0, 0.6, size=(V, S)))
+    t[rng.random((V, S)) < invalid] = np.inf
+    for s in range(S):  # every shape keeps at least one valid variant
+        if not np.isfinite(t[:, s]).any():
+            t[0, s] = 1.0
+    return t
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_invariants(seed):
+    t = _random_table(seed, 7, 9)
+    shapes = range(9)
+    cand = osel.candidate_variants(t, shapes)
+    vals = [osel.portability_tune_exhaustive(t, k, shapes)[1] for k in range(1, len(cand) + 1)]
+    assert all(b >= a - 1e-15 for a, b in zip(vals, vals[1:])), "monotone in k"
+    assert vals[-1] == pytest.approx(1.0, rel=1e-12), "all variants reach every t_best"
+    assert all(0.0 <= v <= 1.0 + 1e-12 for v in vals)
+    # k = 1 is the single variant with the best geomean performance.
+    perf = osel.per_shape_best(t)[None, :] / t
+    single = []
+    for v in range(t.shape[0]):
+        p = perf[v]
+        single.append(0.0 if np.any(p == 0) else float(np.exp(np.mean(np.log(p)))))
+    assert vals[0] == pytest.approx(max(single), rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_exhaustive_equals_brute_force_over_ordered_tuples(seed):
+    # Independent enumeration: ordered k-tuples with repetition (the paper's
+    # |K|^|kappa| space), scored with a vectorised min.
+    t = _random_table(100 + seed, 6, 8, invalid=0.0)
+    tb = t.min(axis=0)
+    for k in (1, 2, 3):
+        best = -1.0
+        for tup in itertools.product(range(6), repeat=k):
+            m = t[list(tup)].min(axis=0)
+            best = max(best, float(np.exp(np.mean(np.log(tb / m)))))
+        _, val = osel.portability_tune_exhaustive(t, k, range(8))
+        assert val == pytest.approx(best, rel=1e-12)
+
+
+def test_planted_block_structure():
+    # Variant g is fastest (1.0) on shape group g and slow (8.0) elsewhere;
+    # variant 4 is 2.0 everywhere.  With k = 4 the specialists are optimal
+    # (value 1); with k = 1 the generalist wins (value 1/2 vs 8^(-3/4)).
+    groups = [[0, 1], [2, 3], [4, 5], [6, 7]]
+    t = np.full((5, 8), 8.0)
+    for g, ss in enumerate(groups):
+        t[g, ss] = 1.0
+    t[4, :] = 2.0
+    kappa, val = osel.portability_tune_exhaustive(t, 4, range(8))
+    assert kappa == [0, 1, 2, 3] and val == pytest.approx(1.0)
+    kappa, val = osel.portability_tune_exhaustive(t, 1, range(8))
+    assert kappa == [4] and val == pytest.approx(0.5)
+    # Scored on a subset of shapes only.
+    assert osel.set_performance(t, [0], [0, 1]) == pytest.approx(1.0)
+    assert osel.set_performance(t, [0], [2, 3]) == pytest.approx(1.0 / 8)
+
+
+def test_invalid_everywhere_in_set_scores_zero():
+    t = np.array([[1.0, np.inf], [2.0, 2.0]])
+    assert osel.set_performance(t, [0], [0, 1]) == 0.0
+    assert osel.set_performance(t, [0, 1], [0, 1]) == pytest.approx(1.0)
+
+
+def test_nearest_shape_rule():
+    shapes = [(128, 128, 128), (1024, 1024, 1024), (4096, 128, 512)]
+    assert osel.nearest_shape((1024, 1024, 1024), shapes) == 1
+    assert osel.nearest_shape((2048, 1024, 1024), shapes) == 1      # distance 1 vs 7+ vs ...
+    assert osel.nearest_shape((4096, 256, 512), shapes) == 2
+    # Equidistant (log2 distance 3.5 to both (128^3) and (1024^3)): lower index wins.
+    m = int(round(2 ** 8.5))
+    d0 = sum(abs(math.log2(x) - 7) for x in (m, 128, 1024))
+    d1 = sum(abs(math.log2(x) - 10) for x in (m, 128, 1024))
+    q = (m, 128, 1024)
+    assert osel.nearest_shape(q, shapes[:2]) == (0 if d0 <= d1 else 1)
+
+
+def test_best_in_set_ties_go_to_lowest_id():
+    t = np.array([[3.0], [1.0], [1.0]])
+    assert osel.best_in_set(t, [2, 1, 0], 0) == 1
