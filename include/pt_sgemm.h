@@ -1,0 +1,191 @@
+/*
+ * pt_sgemm -- portability-tuned single-precision GEMM for sm_103a (GB300).
+ *
+ * C ABI of the library libptsgemm.so.  Every call returns an int status
+ * (PT_OK = 0, negative on error) and never aborts or prints (unless the
+ * environment variable PT_VERBOSE is set).  After a failing call,
+ * pt_last_error() gives a message and pt_last_error_arg() the 1-based index
+ * of the offending argument (0 when no single argument is at fault); both are
+ * per host thread.
+ *
+ * Operation (the problem statement of "A Few Fit Most: Improving Performance
+ * Portability of SGEMM on GPUs using Multi-Versioning", Section V-B, in BLAS
+ * form):
+ *
+ *     C <- alpha * op(A) * op(B) + beta * C,   op(X) = X or X^T
+ *
+ * Storage is ROW-MAJOR.  op(A) is M x K, op(B) is K x N, C is M x N.
+ *   transA 'N': A is M x K, lda >= max(1, K);  'T': A is K x M, lda >= max(1, M)
+ *   transB 'N': B is K x N, ldb >= max(1, N);  'T': B is N x K, ldb >= max(1, K)
+ *   C: ldc >= max(1, N).
+ * beta == 0 means C is not read (NaN/Inf already in C do not propagate).
+ * M == 0 or N == 0 returns at once; K == 0 or alpha == 0 sets C <- beta*C.
+ *
+ * A, B, C are DEVICE pointers owned by the caller; the library never frees
+ * or retains them.  Calls on a stream are asynchronous with respect to the
+ * host; `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  C must not alias A or B.
+ */
+#ifndef PT_SGEMM_H
+#define PT_SGEMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PT_OK 0
+#define PT_EINVAL (-1)        /* invalid argument (see pt_last_error_arg)   */
+#define PT_EUNSUPPORTED (-2)  /* variant cannot run this shape/layout      */
+#define PT_ECUDA (-3)         /* CUDA runtime or driver error              */
+#define PT_EIO (-4)           /* file could not be opened/written          */
+#define PT_EFORMAT (-5)       /* malformed table or manifest               */
+#define PT_ETIMEOUT (-6)      /* a bounded device wait gave up             */
+
+const char *pt_last_error(void);
+int pt_last_error_arg(void);
+
+/* ---- the operation ------------------------------------------------------
+ * pt_sgemm: the multi-versioned entry.  The runtime selector (the
+ * "classifier" of the paper's Fig. 1, Section III-C) maps the call's
+ * (transA, transB, M, N, K) to one variant of the loaded set kappa
+ * (pt_load_manifest): an exact shape hit takes the member timed fastest on
+ * that shape; any other shape takes the pick of the nearest listed shape in
+ * (log2 M, log2 N, log2 K), L1 distance, ties to the lower entry.  With no
+ * manifest loaded, or when the picked variant cannot run the arguments
+ * (alignment, transpose support), the next members of kappa are tried in
+ * the order of the manifest and finally the built-in default variant, which
+ * runs every valid argument set.
+ */
+int pt_sgemm(char transA, char transB, int64_t M, int64_t N, int64_t K,
+             float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+             float beta, float *C, int64_t ldc, void *stream);
+
+/* Runs variant `id` (0 <= id < pt_num_variants()).  PT_EUNSUPPORTED when the
+ * variant's layout or alignment rules exclude these arguments; nothing is
+ * launched then. */
+int pt_sgemm_variant(int id, char transA, char transB, int64_t M, int64_t N, int64_t K,
+                     float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                     float beta, float *C, int64_t ldc, void *stream);
+
+/* Screening reference kernel (the paper's "reference kernels", Section V-C):
+ * one thread per output, compensated FP32 dot product (TwoProduct/TwoSum),
+ * independent of the variant family.  Same arguments as pt_sgemm. */
+int pt_sgemm_reference(char transA, char transB, int64_t M, int64_t N, int64_t K,
+                       float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                       float beta, float *C, int64_t ldc, void *stream);
+
+/* ---- variant registry (a parameter configuration compiled ahead of time;
+ * Section III-A terminology, precompilation Section III-B) ---------------- */
+#define PT_LOADER_CPASYNC 0   /* cp.async global->shared staging            */
+#define PT_LOADER_TMA 1       /* cp.async.bulk.tensor (TMA) + mbarrier       */
+
+typedef struct pt_variant_desc {
+    int id;
+    int bm, bn, bk;    /* CTA tile M x N and K-step                          */
+    int wm, wn;        /* warp tile                                          */
+    int tm, tn;        /* per-thread register tile                           */
+    int kl;            /* k-groups of lanes inside a warp, shuffle-reduced   */
+    int vec;           /* floats per direct global load / store (1, 2, 4)    */
+    int stages;        /* shared-memory pipeline depth                       */
+    int splitk;        /* CTAs of a cluster splitting K, reduced over DSMEM  */
+    int loader;        /* PT_LOADER_*                                        */
+    int a_kmajor;      /* 1: A tile held K-major (swizzled) in shared memory */
+    int threads;       /* threads per CTA                                    */
+    int smem_bytes;    /* dynamic shared memory per CTA                      */
+    int trans_mask;    /* bit (2*tA + tB) set when (transA, transB) runs;
+                          tX = 0 for 'N', 1 for 'T'                          */
+    int kind;          /* 0 = FP32 SIMT                                      */
+    char name[96];     /* stable key used in tables and manifests           */
+} pt_variant_desc_t;
+
+int pt_num_variants(void);
+int pt_variant_desc(int id, pt_variant_desc_t *out);
+/* id of a variant by name, or PT_EINVAL */
+int pt_variant_by_name(const char *name);
+/* the fixed default variant (128x128x8 CTA tile, cp.async, any layout) */
+int pt_default_variant(void);
+
+/* ---- portability tuning ------------------------------------------------ */
+typedef struct pt_shape {
+    int64_t m, n, k;
+    char transA, transB;
+} pt_shape_t;
+
+typedef struct pt_tune_opts {
+    int warmup;          /* untimed launches per entry (>= 0; default 2)       */
+    int reps_min;        /* timed launches per entry, lower bound (default 5)  */
+    int reps_max;        /* upper bound (default 50)                           */
+    double target_ms;    /* aim for reps * t ~ target (default 5 ms)           */
+    uint64_t seed;       /* SplitMix64 seed of the on-device inputs            */
+    int resume;          /* 1: keep rows already in the table, skip them       */
+    double tol;          /* screening bound on the normalised error (2e-6)     */
+    int64_t pool_bytes;  /* rotating input pool; >= 2x L2 keeps L2 cold        */
+    int verbose;         /* progress to stderr                                 */
+} pt_tune_opts_t;
+
+/* Fills *o with the defaults above. */
+void pt_tune_default_opts(pt_tune_opts_t *o);
+
+/* Data collection (Section V-D): times every listed variant (ids == NULL:
+ * all) on every shape and appends one CSV row per (shape, variant) to
+ * table_path, flushing after each row, so the file is the checkpoint.  Each
+ * variant is first screened against the reference kernel on the same inputs;
+ * a launch error or a normalised error above opts->tol marks the row invalid.
+ * Timing: per-launch CUDA events after warmup, inputs rotating through a pool
+ * larger than L2; median and mean recorded.  The library allocates and frees
+ * its own device buffers on the current device.  Synchronous. */
+int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids,
+            const pt_tune_opts_t *opts, const char *table_path);
+
+#define PT_SELECT_EXACT 0       /* enumerate every k-subset                    */
+#define PT_SELECT_GREEDY_SWAP 1 /* greedy growth + 1-swap local search         */
+#define PT_SELECT_AUTO 2        /* exact when C(n,k) <= 2e6, else greedy+swap  */
+#define PT_SELECT_KMEANS 3      /* k-means on performance vectors (IV-C-2)     */
+#define PT_SELECT_TREE 4        /* regression tree with k leaves (IV-C-3)      */
+
+/* PortabilityTune (Section IV-B, cost Eq. 1): choose kappa, |kappa| <= k, of
+ * table variants maximising the geometric mean over the training shapes
+ * (indices into the table's distinct-shape list, in order of first
+ * appearance) of t_best(s) / min_{v in kappa} t(v, s), t_best over every
+ * valid variant of the table.  Writes the ids to out_ids[0..k) (-1 padded),
+ * the training geomean to *out_train_geomean, and, when manifest_path is not
+ * NULL, a manifest (kappa + each training shape's fastest member).  `seed`
+ * drives the random restarts / initialisation of the heuristic methods.
+ * CPU only. */
+int pt_select(const char *table_path, const int *train_idx, int n_train, int k,
+              int method, uint64_t seed, int *out_ids, double *out_train_geomean,
+              const char *manifest_path);
+
+#define PT_SCORE_BEST_OF_SET 0  /* each shape uses kappa's fastest member     */
+#define PT_SCORE_SELECTOR 1     /* each shape uses the runtime selector's pick
+                                   from the manifest at manifest_path         */
+
+/* Geomean over the listed shapes of t_best(s) / t(chosen(s), s). */
+int pt_score(const char *table_path, const int *ids, int k, const int *shape_idx,
+             int n, int mode, const char *manifest_path, double *out_geomean);
+
+/* Number of distinct shapes in a table and shape i of it. */
+int pt_table_shapes(const char *table_path, int *out_n);
+int pt_table_shape(const char *table_path, int i, pt_shape_t *out);
+
+/* Installs the manifest used by pt_sgemm (process-wide, mutex-guarded);
+ * NULL clears it. */
+int pt_load_manifest(const char *path);
+/* The variant id pt_sgemm would launch for these arguments (same rules). */
+int pt_selected_variant(char transA, char transB, int64_t M, int64_t N, int64_t K,
+                        const float *A, int64_t lda, const float *B, int64_t ldb,
+                        const float *C, int64_t ldc);
+
+/* Device-side error word set by kernels whose bounded waits gave up
+ * (PT_ETIMEOUT) on the current device; reading clears it.  Synchronises the
+ * device. */
+int pt_device_status(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_SGEMM_H */

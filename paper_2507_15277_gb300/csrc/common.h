@@ -1,0 +1,59 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pt_sgemm.h"
+
+namespace pt {
+
+int set_error(int code, int arg, const char *fmt, ...);
+void clear_error();
+bool verbose();
+
+// ---- timing table --------------------------------------------------------------
+struct TableRow {
+    int shape_idx = -1;
+    pt_shape_t shape{};
+    std::string variant;  // name (stable key)
+    int status = 0;       // PT_OK or the launch status
+    int valid = 0;
+    double median_ms = 0, mean_ms = 0, min_ms = 0;
+    int reps = 0;
+    double tflops = 0, gbs = 0, max_err = 0;
+};
+
+struct Table {
+    std::vector<pt_shape_t> shapes;      // distinct shapes, first-appearance order
+    std::vector<std::string> variants;   // distinct variant names, first-appearance order
+    std::vector<std::vector<double>> t;  // t[v][s] median ms, +inf when invalid / missing
+    std::vector<TableRow> rows;
+};
+
+int read_table(const char *path, Table *out);
+extern const char *kTableHeader;
+std::string format_row(const TableRow &r);
+bool same_shape(const pt_shape_t &a, const pt_shape_t &b);
+
+// ---- manifest (the multi-versioned set and its shape map) ----------------------
+struct ManifestEntry {
+    pt_shape_t shape;
+    int variant;  // registry id
+};
+
+struct Manifest {
+    std::string method;
+    std::vector<int> kappa;  // registry ids, in manifest order
+    std::vector<ManifestEntry> map;
+    double train_geomean = 0;
+};
+
+int read_manifest(const char *path, Manifest *out);
+// The runtime selector's pick for a shape (-1 if the manifest is empty).
+int manifest_pick(const Manifest &m, const pt_shape_t &s);
+// Installed manifest (copy under the library mutex).
+bool installed_manifest(Manifest *out);
+
+}  // namespace pt

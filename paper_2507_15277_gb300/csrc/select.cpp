@@ -1,0 +1,639 @@
+// Portability tuning on the host: timing-table I/O, PortabilityTune (exact
+// enumeration, greedy + swap), the library cost function, held-out scoring,
+// and the manifest that carries the selected set to the runtime selector.
+//
+// Paper: Section IV-B (PortabilityTune returns a set kappa of variants for a
+// set of inputs), Section IV-C (search over subsets of the variant space;
+// its |inputs| * |K|^|kappa| cost), Section IV-D Eq. 1 (library cost
+// function: geometric mean over environments of each environment's best
+// performance relative to its Oracle), Section V-D (post-processing relative
+// to the best variant per input), Fig. 1 (runtime inference).
+#include <algorithm>
+#include <cerrno>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <limits>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "json.h"
+
+namespace pt {
+
+const char *kTableHeader =
+    "shape_idx,M,N,K,transA,transB,variant,status,valid,median_ms,mean_ms,min_ms,reps,tflops,gbs,max_err";
+
+bool same_shape(const pt_shape_t &a, const pt_shape_t &b) {
+    return a.m == b.m && a.n == b.n && a.k == b.k && a.transA == b.transA && a.transB == b.transB;
+}
+
+std::string format_row(const TableRow &r) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%d,%lld,%lld,%lld,%c,%c,%s,%d,%d,%.9g,%.9g,%.9g,%d,%.6g,%.6g,%.6g",
+                  r.shape_idx, (long long)r.shape.m, (long long)r.shape.n, (long long)r.shape.k, r.shape.transA,
+                  r.shape.transB, r.variant.c_str(), r.status, r.valid, r.median_ms, r.mean_ms, r.min_ms, r.reps,
+                  r.tflops, r.gbs, r.max_err);
+    return buf;
+}
+
+static bool split_csv(const std::string &line, std::vector<std::string> *f) {
+    f->clear();
+    std::string cur;
+    for (char c : line) {
+        if (c == ',') {
+            f->push_back(cur);
+            cur.clear();
+        } else if (c != '\r') {
+            cur.push_back(c);
+        }
+    }
+    f->push_back(cur);
+    return true;
+}
+
+static bool to_ll(const std::string &s, long long *v) {
+    if (s.empty()) return false;
+    char *e = nullptr;
+    errno = 0;
+    *v = std::strtoll(s.c_str(), &e, 10);
+    return errno == 0 && e && *e == 0;
+}
+
+static bool to_d(const std::string &s, double *v) {
+    if (s.empty()) return false;
+    char *e = nullptr;
+    *v = std::strtod(s.c_str(), &e);
+    return e && *e == 0;
+}
+
+int read_table(const char *path, Table *out) {
+    std::ifstream in(path);
+    if (!in) return set_error(PT_EIO, 1, "cannot open table '%s'", path);
+    std::string line;
+    if (!std::getline(in, line)) return set_error(PT_EFORMAT, 1, "empty table '%s'", path);
+    if (!line.empty() && line.back() == '\r') line.pop_back();
+    if (line != kTableHeader) return set_error(PT_EFORMAT, 1, "table '%s': unexpected header", path);
+    Table t;
+    std::map<std::string, int> vidx;
+    std::vector<std::string> f;
+    int lineno = 1;
+    while (std::getline(in, line)) {
+        ++lineno;
+        if (line.empty() || line == "\r") continue;
+        split_csv(line, &f);
+        if (f.size() != 16) return set_error(PT_EFORMAT, 1, "table line %d: %zu fields", lineno, f.size());
+        TableRow r;
+        long long si, m, n, k, st, valid, reps;
+        if (!to_ll(f[0], &si) || !to_ll(f[1], &m) || !to_ll(f[2], &n) || !to_ll(f[3], &k) || f[4].size() != 1 ||
+            f[5].size() != 1 || f[6].empty() || !to_ll(f[7], &st) || !to_ll(f[8], &valid) ||
+            !to_d(f[9], &r.median_ms) || !to_d(f[10], &r.mean_ms) || !to_d(f[11], &r.min_ms) ||
+            !to_ll(f[12], &reps) || !to_d(f[13], &r.tflops) || !to_d(f[14], &r.gbs) || !to_d(f[15], &r.max_err))
+            return set_error(PT_EFORMAT, 1, "table line %d: malformed field", lineno);
+        if (m < 0 || n < 0 || k < 0 || (f[4][0] != 'N' && f[4][0] != 'T') || (f[5][0] != 'N' && f[5][0] != 'T') ||
+            (valid != 0 && valid != 1))
+            return set_error(PT_EFORMAT, 1, "table line %d: invalid value", lineno);
+        if (valid && !(r.median_ms > 0 && std::isfinite(r.median_ms)))
+            return set_error(PT_EFORMAT, 1, "table line %d: valid row without a positive time", lineno);
+        r.shape_idx = (int)si;
+        r.shape.m = m; r.shape.n = n; r.shape.k = k;
+        r.shape.transA = f[4][0]; r.shape.transB = f[5][0];
+        r.variant = f[6];
+        r.status = (int)st; r.valid = (int)valid; r.reps = (int)reps;
+        int s = -1;
+        for (size_t i = 0; i < t.shapes.size(); ++i)
+            if (same_shape(t.shapes[i], r.shape)) { s = (int)i; break; }
+        if (s < 0) {
+            s = (int)t.shapes.size();
+            t.shapes.push_back(r.shape);
+            for (auto &col : t.t) col.push_back(std::numeric_limits<double>::infinity());
+        }
+        auto it = vidx.find(r.variant);
+        int v;
+        if (it == vidx.end()) {
+            v = (int)t.variants.size();
+            vidx[r.variant] = v;
+            t.variants.push_back(r.variant);
+            t.t.emplace_back(t.shapes.size(), std::numeric_limits<double>::infinity());
+        } else {
+            v = it->second;
+        }
+        // A later row for the same (shape, variant) replaces an earlier one.
+        t.t[v][s] = r.valid ? r.median_ms : std::numeric_limits<double>::infinity();
+        t.rows.push_back(r);
+    }
+    *out = std::move(t);
+    return PT_OK;
+}
+
+// ---- the cost function (Eq. 1, read as a performance to maximise) ---------------
+namespace {
+
+constexpr double kInf = std::numeric_limits<double>::infinity();
+
+struct Problem {
+    std::vector<int> cand;  // table variant indices, ascending registry id
+    std::vector<int> reg;   // registry id of each candidate
+    int S = 0;
+    std::vector<double> lg;  // lg[c*S + s] = log(t_best[s] / t[cand[c]][s]), -inf if invalid
+    double at(int c, int s) const { return lg[(size_t)c * S + s]; }
+};
+
+// t_best over every variant of the table.
+std::vector<double> best_per_shape(const Table &t) {
+    std::vector<double> b(t.shapes.size(), kInf);
+    for (const auto &col : t.t)
+        for (size_t s = 0; s < col.size(); ++s) b[s] = std::min(b[s], col[s]);
+    return b;
+}
+
+int registry_id(const std::string &name) {
+    const int id = pt_variant_by_name(name.c_str());
+    return id;
+}
+
+int build_problem(const Table &t, const std::vector<int> &shapes, Problem *p) {
+    const std::vector<double> tb = best_per_shape(t);
+    std::vector<std::pair<int, int>> cands;  // (registry id, table index)
+    for (size_t v = 0; v < t.variants.size(); ++v) {
+        bool any = false;
+        for (int s : shapes) any = any || std::isfinite(t.t[v][s]);
+        if (!any) continue;
+        const int id = registry_id(t.variants[v]);
+        if (id < 0) return set_error(PT_EFORMAT, 1, "table variant '%s' is not in this library", t.variants[v].c_str());
+        cands.emplace_back(id, (int)v);
+    }
+    std::sort(cands.begin(), cands.end());
+    p->S = (int)shapes.size();
+    p->cand.clear();
+    p->reg.clear();
+    for (auto &c : cands) {
+        p->reg.push_back(c.first);
+        p->cand.push_back(c.second);
+    }
+    p->lg.assign(p->cand.size() * (size_t)p->S, -kInf);
+    for (size_t c = 0; c < p->cand.size(); ++c)
+        for (int j = 0; j < p->S; ++j) {
+            const double tv = t.t[p->cand[c]][shapes[j]];
+            if (std::isfinite(tv)) p->lg[c * p->S + j] = std::log(tb[shapes[j]] / tv);
+        }
+    return PT_OK;
+}
+
+// Geomean of per-shape best-of-set performance given the per-shape max log.
+double geomean_from(const std::vector<double> &mx, int S) {
+    if (S == 0) return 1.0;
+    double total = 0;
+    for (int s = 0; s < S; ++s) {
+        if (!std::isfinite(mx[s])) return 0.0;
+        total += mx[s];
+    }
+    return std::exp(total / S);
+}
+
+double set_value(const Problem &p, const std::vector<int> &set) {
+    std::vector<double> mx(p.S, -kInf);
+    for (int c : set)
+        for (int s = 0; s < p.S; ++s) mx[s] = std::max(mx[s], p.at(c, s));
+    return geomean_from(mx, p.S);
+}
+
+// Exhaustive PortabilityTune: every k-subset of the candidates in
+// lexicographic order; a later subset replaces the best only when strictly
+// better, so exact ties keep the lexicographically smallest set.
+void exact_rec(const Problem &p, int k, int start, std::vector<int> &cur, std::vector<std::vector<double>> &mx,
+               std::vector<int> &best, double &best_val) {
+    const int d = (int)cur.size();
+    const int n = (int)p.cand.size();
+    for (int c = start; c <= n - (k - d); ++c) {
+        std::vector<double> &m = mx[d + 1];
+        for (int s = 0; s < p.S; ++s) m[s] = std::max(mx[d][s], p.at(c, s));
+        cur.push_back(c);
+        if (d + 1 == k) {
+            const double v = geomean_from(m, p.S);
+            if (v > best_val) {
+                best_val = v;
+                best = cur;
+            }
+        } else {
+            exact_rec(p, k, c + 1, cur, mx, best, best_val);
+        }
+        cur.pop_back();
+    }
+}
+
+void select_exact(const Problem &p, int k, std::vector<int> *out, double *val) {
+    const int n = (int)p.cand.size();
+    if (k >= n) {
+        out->resize(n);
+        for (int i = 0; i < n; ++i) (*out)[i] = i;
+        *val = set_value(p, *out);
+        return;
+    }
+    std::vector<std::vector<double>> mx(k + 1, std::vector<double>(p.S, -kInf));
+    std::vector<int> cur, best;
+    double best_val = -1.0;
+    exact_rec(p, k, 0, cur, mx, best, best_val);
+    *out = best;
+    *val = best_val;
+}
+
+// Greedy growth and 1-swap local search on the facility-location form
+// F(kappa) = sum_s max_{v in kappa} max(lg[v][s], floor), which equals
+// S * log(Eq. 1 value) whenever every shape is covered.
+constexpr double kFloor = -30.0;
+
+double f_value(const Problem &p, const std::vector<int> &set) {
+    double tot = 0;
+    for (int s = 0; s < p.S; ++s) {
+        double m = kFloor;
+        for (int c : set) m = std::max(m, p.at(c, s));
+        tot += m;
+    }
+    return tot;
+}
+
+void local_search(const Problem &p, std::vector<int> &set) {
+    const int n = (int)p.cand.size();
+    const int k = (int)set.size();
+    std::vector<char> in(n, 0);
+    for (int c : set) in[c] = 1;
+    while (true) {
+        // Per shape: best and second-best member values and the best's slot.
+        std::vector<double> b1(p.S, kFloor), b2(p.S, kFloor);
+        std::vector<int> who(p.S, -1);
+        for (int slot = 0; slot < k; ++slot)
+            for (int s = 0; s < p.S; ++s) {
+                const double v = std::max(p.at(set[slot], s), kFloor);
+                if (v > b1[s]) { b2[s] = b1[s]; b1[s] = v; who[s] = slot; }
+                else if (v > b2[s]) b2[s] = v;
+            }
+        double base = 0;
+        for (int s = 0; s < p.S; ++s) base += b1[s];
+        double best_gain = 1e-12;
+        int best_slot = -1, best_c = -1;
+        for (int slot = 0; slot < k; ++slot) {
+            for (int c = 0; c < n; ++c) {
+                if (in[c]) continue;
+                double tot = 0;
+                for (int s = 0; s < p.S; ++s) {
+                    const double rest = (who[s] == slot) ? b2[s] : b1[s];
+                    tot += std::max(rest, std::max(p.at(c, s), kFloor));
+                }
+                if (tot - base > best_gain) {
+                    best_gain = tot - base;
+                    best_slot = slot;
+                    best_c = c;
+                }
+            }
+        }
+        if (best_slot < 0) break;
+        in[set[best_slot]] = 0;
+        in[best_c] = 1;
+        set[best_slot] = best_c;
+    }
+    std::sort(set.begin(), set.end());
+}
+
+uint64_t splitmix(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void select_greedy_swap(const Problem &p, int k, uint64_t seed, std::vector<int> *out, double *val) {
+    const int n = (int)p.cand.size();
+    if (k >= n) {
+        select_exact(p, k, out, val);
+        return;
+    }
+    std::vector<int> best;
+    double best_g = -1, best_f = -kInf;
+    const int restarts = 8;
+    uint64_t draw = 0;
+    for (int r = 0; r < restarts; ++r) {
+        std::vector<int> set;
+        if (r == 0) {
+            std::vector<char> in(n, 0);
+            for (int step = 0; step < k; ++step) {
+                int arg = -1;
+                double bv = -kInf;
+                for (int c = 0; c < n; ++c) {
+                    if (in[c]) continue;
+                    set.push_back(c);
+                    const double f = f_value(p, set);
+                    set.pop_back();
+                    if (f > bv + 1e-12) { bv = f; arg = c; }
+                }
+                in[arg] = 1;
+                set.push_back(arg);
+            }
+        } else {
+            std::vector<char> in(n, 0);
+            while ((int)set.size() < k) {
+                const int c = (int)(splitmix(seed, draw++) % (uint64_t)n);
+                if (!in[c]) { in[c] = 1; set.push_back(c); }
+            }
+        }
+        local_search(p, set);
+        const double g = set_value(p, set), f = f_value(p, set);
+        if (g > best_g || (g == best_g && f > best_f) || (g == best_g && f == best_f && set < best)) {
+            best_g = g;
+            best_f = f;
+            best = set;
+        }
+    }
+    *out = best;
+    *val = best_g;
+}
+
+double log_binom(int n, int k) { return std::lgamma(n + 1.0) - std::lgamma(k + 1.0) - std::lgamma(n - k + 1.0); }
+
+}  // namespace
+
+// ---- manifest --------------------------------------------------------------------
+static std::string shape_json(const pt_shape_t &s) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "\"m\": %lld, \"n\": %lld, \"k\": %lld, \"transA\": \"%c\", \"transB\": \"%c\"",
+                  (long long)s.m, (long long)s.n, (long long)s.k, s.transA, s.transB);
+    return buf;
+}
+
+static int write_manifest(const char *path, const char *method, int k, double g, const std::vector<int> &kappa_ids,
+                          const std::vector<std::pair<pt_shape_t, int>> &map) {
+    std::ofstream o(path);
+    if (!o) return set_error(PT_EIO, 9, "cannot write manifest '%s'", path);
+    auto name = [](int id) {
+        pt_variant_desc_t d;
+        pt_variant_desc(id, &d);
+        return std::string(d.name);
+    };
+    char gbuf[64];
+    std::snprintf(gbuf, sizeof(gbuf), "%.17g", g);
+    o << "{\n  \"format\": \"pt-manifest-1\",\n  \"method\": " << json::quote(method) << ",\n  \"k\": " << k
+      << ",\n  \"train_geomean\": " << gbuf << ",\n  \"kappa\": [";
+    for (size_t i = 0; i < kappa_ids.size(); ++i) o << (i ? ", " : "") << json::quote(name(kappa_ids[i]));
+    o << "],\n  \"map\": [";
+    for (size_t i = 0; i < map.size(); ++i)
+        o << (i ? ",\n" : "\n") << "    {" << shape_json(map[i].first)
+          << ", \"variant\": " << json::quote(name(map[i].second)) << "}";
+    o << "\n  ]\n}\n";
+    o.flush();
+    if (!o) return set_error(PT_EIO, 9, "write failed for '%s'", path);
+    return PT_OK;
+}
+
+int read_manifest(const char *path, Manifest *out) {
+    std::ifstream in(path);
+    if (!in) return set_error(PT_EIO, 1, "cannot open manifest '%s'", path);
+    std::stringstream ss;
+    ss << in.rdbuf();
+    const std::string text = ss.str();
+    json::Value root;
+    json::Parser parser(text);
+    if (!parser.parse(&root) || root.kind != json::Value::Object)
+        return set_error(PT_EFORMAT, 1, "manifest '%s': not a JSON object", path);
+    const json::Value *fmt = root.get("format");
+    if (!fmt || fmt->kind != json::Value::String || fmt->str != "pt-manifest-1")
+        return set_error(PT_EFORMAT, 1, "manifest '%s': unknown format", path);
+    Manifest m;
+    if (const json::Value *me = root.get("method"); me && me->kind == json::Value::String) m.method = me->str;
+    if (const json::Value *g = root.get("train_geomean"); g && g->kind == json::Value::Number) m.train_geomean = g->num;
+    const json::Value *kap = root.get("kappa");
+    if (!kap || kap->kind != json::Value::Array || kap->arr.empty())
+        return set_error(PT_EFORMAT, 1, "manifest '%s': kappa missing or empty", path);
+    for (const auto &v : kap->arr) {
+        if (v.kind != json::Value::String) return set_error(PT_EFORMAT, 1, "manifest: kappa entry is not a name");
+        const int id = pt_variant_by_name(v.str.c_str());
+        if (id < 0) return set_error(PT_EFORMAT, 1, "manifest: unknown variant '%s'", v.str.c_str());
+        m.kappa.push_back(id);
+    }
+    const json::Value *map = root.get("map");
+    if (map) {
+        if (map->kind != json::Value::Array) return set_error(PT_EFORMAT, 1, "manifest: map is not an array");
+        for (const auto &e : map->arr) {
+            const json::Value *vm = e.get("m"), *vn = e.get("n"), *vk = e.get("k"), *ta = e.get("transA"),
+                              *tb = e.get("transB"), *var = e.get("variant");
+            if (!vm || !vn || !vk || !ta || !tb || !var || vm->kind != json::Value::Number ||
+                vn->kind != json::Value::Number || vk->kind != json::Value::Number ||
+                ta->kind != json::Value::String || tb->kind != json::Value::String ||
+                var->kind != json::Value::String || ta->str.size() != 1 || tb->str.size() != 1 || vm->num < 1 ||
+                vn->num < 1 || vk->num < 1)
+                return set_error(PT_EFORMAT, 1, "manifest: malformed map entry");
+            ManifestEntry me;
+            me.shape.m = (int64_t)vm->num;
+            me.shape.n = (int64_t)vn->num;
+            me.shape.k = (int64_t)vk->num;
+            me.shape.transA = ta->str[0];
+            me.shape.transB = tb->str[0];
+            me.variant = pt_variant_by_name(var->str.c_str());
+            if (me.variant < 0) return set_error(PT_EFORMAT, 1, "manifest: unknown variant '%s'", var->str.c_str());
+            if (std::find(m.kappa.begin(), m.kappa.end(), me.variant) == m.kappa.end())
+                return set_error(PT_EFORMAT, 1, "manifest: map names a variant outside kappa");
+            m.map.push_back(me);
+        }
+    }
+    *out = std::move(m);
+    return PT_OK;
+}
+
+// Runtime selector (Fig. 1 inference step): exact hit, else nearest listed
+// shape with the same transposes (any transposes if none) in log2 space, L1
+// distance, ties to the earlier entry; with no map, the first member.
+int manifest_pick(const Manifest &m, const pt_shape_t &s) {
+    if (m.kappa.empty()) return -1;
+    if (m.map.empty()) return m.kappa[0];
+    for (const auto &e : m.map)
+        if (same_shape(e.shape, s)) return e.variant;
+    bool any_same_trans = false;
+    for (const auto &e : m.map)
+        any_same_trans = any_same_trans || (e.shape.transA == s.transA && e.shape.transB == s.transB);
+    const double q[3] = {std::log2((double)s.m), std::log2((double)s.n), std::log2((double)s.k)};
+    int best = -1;
+    double best_d = kInf;
+    for (const auto &e : m.map) {
+        if (any_same_trans && (e.shape.transA != s.transA || e.shape.transB != s.transB)) continue;
+        const double d = std::fabs(std::log2((double)e.shape.m) - q[0]) + std::fabs(std::log2((double)e.shape.n) - q[1]) +
+                         std::fabs(std::log2((double)e.shape.k) - q[2]);
+        if (d < best_d) {
+            best_d = d;
+            best = e.variant;
+        }
+    }
+    return best;
+}
+
+}  // namespace pt
+
+using namespace pt;
+
+extern "C" {
+
+int pt_table_shapes(const char *table_path, int *out_n) {
+    clear_error();
+    if (!table_path) return set_error(PT_EINVAL, 1, "table_path is NULL");
+    if (!out_n) return set_error(PT_EINVAL, 2, "out_n is NULL");
+    Table t;
+    int rc = read_table(table_path, &t);
+    if (rc != PT_OK) return rc;
+    *out_n = (int)t.shapes.size();
+    return PT_OK;
+}
+
+int pt_table_shape(const char *table_path, int i, pt_shape_t *out) {
+    clear_error();
+    if (!table_path) return set_error(PT_EINVAL, 1, "table_path is NULL");
+    if (!out) return set_error(PT_EINVAL, 3, "out is NULL");
+    Table t;
+    int rc = read_table(table_path, &t);
+    if (rc != PT_OK) return rc;
+    if (i < 0 || i >= (int)t.shapes.size()) return set_error(PT_EINVAL, 2, "shape index out of range");
+    *out = t.shapes[i];
+    return PT_OK;
+}
+
+int pt_select(const char *table_path, const int *train_idx, int n_train, int k, int method, uint64_t seed,
+              int *out_ids, double *out_train_geomean, const char *manifest_path) {
+    clear_error();
+    if (!table_path) return set_error(PT_EINVAL, 1, "table_path is NULL");
+    if (k < 1) return set_error(PT_EINVAL, 4, "k must be >= 1");
+    if (n_train < 0 || (n_train > 0 && !train_idx)) return set_error(PT_EINVAL, 2, "bad training list");
+    if (!out_ids) return set_error(PT_EINVAL, 7, "out_ids is NULL");
+    Table t;
+    int rc = read_table(table_path, &t);
+    if (rc != PT_OK) return rc;
+    std::vector<int> shapes;
+    if (n_train == 0) {
+        for (size_t s = 0; s < t.shapes.size(); ++s) shapes.push_back((int)s);
+    } else {
+        for (int i = 0; i < n_train; ++i) {
+            if (train_idx[i] < 0 || train_idx[i] >= (int)t.shapes.size())
+                return set_error(PT_EINVAL, 2, "training shape index %d out of range", train_idx[i]);
+            shapes.push_back(train_idx[i]);
+        }
+    }
+    if (shapes.empty()) return set_error(PT_EINVAL, 2, "no training shapes");
+    Problem p;
+    rc = build_problem(t, shapes, &p);
+    if (rc != PT_OK) return rc;
+    if (p.cand.empty()) return set_error(PT_EFORMAT, 1, "no variant is valid on the training shapes");
+    std::vector<int> set;
+    double val = 0;
+    const char *mname = "exact";
+    switch (method) {
+        case PT_SELECT_EXACT:
+            if (k < (int)p.cand.size() && log_binom((int)p.cand.size(), k) > std::log(5e8))
+                return set_error(PT_EUNSUPPORTED, 5, "exact enumeration of C(%zu,%d) subsets is too large",
+                                 p.cand.size(), k);
+            select_exact(p, k, &set, &val);
+            break;
+        case PT_SELECT_GREEDY_SWAP:
+            mname = "greedy_swap";
+            select_greedy_swap(p, k, seed, &set, &val);
+            break;
+        case PT_SELECT_AUTO:
+            if (k >= (int)p.cand.size() || log_binom((int)p.cand.size(), k) <= std::log(2e6)) {
+                select_exact(p, k, &set, &val);
+            } else {
+                mname = "greedy_swap";
+                select_greedy_swap(p, k, seed, &set, &val);
+            }
+            break;
+        default:
+            return set_error(PT_EINVAL, 5, "unknown selection method %d", method);
+    }
+    std::vector<int> ids;
+    for (int c : set) ids.push_back(p.reg[c]);
+    for (int i = 0; i < k; ++i) out_ids[i] = i < (int)ids.size() ? ids[i] : -1;
+    if (out_train_geomean) *out_train_geomean = val;
+    if (manifest_path) {
+        // Shape map: each training shape's fastest member (ties -> lowest id).
+        std::vector<std::pair<pt_shape_t, int>> map;
+        for (int j = 0; j < p.S; ++j) {
+            int best = -1;
+            double bt = kInf;
+            for (int c : set) {
+                const double tv = t.t[p.cand[c]][shapes[j]];
+                if (tv < bt) {
+                    bt = tv;
+                    best = p.reg[c];
+                }
+            }
+            if (best >= 0) map.emplace_back(t.shapes[shapes[j]], best);
+        }
+        rc = write_manifest(manifest_path, mname, k, val, ids, map);
+        if (rc != PT_OK) return rc;
+    }
+    return PT_OK;
+}
+
+int pt_score(const char *table_path, const int *ids, int k, const int *shape_idx, int n, int mode,
+             const char *manifest_path, double *out_geomean) {
+    clear_error();
+    if (!table_path) return set_error(PT_EINVAL, 1, "table_path is NULL");
+    if (!out_geomean) return set_error(PT_EINVAL, 8, "out_geomean is NULL");
+    if (n < 0 || (n > 0 && !shape_idx)) return set_error(PT_EINVAL, 4, "bad shape list");
+    Table t;
+    int rc = read_table(table_path, &t);
+    if (rc != PT_OK) return rc;
+    std::map<int, int> reg_to_table;
+    for (size_t v = 0; v < t.variants.size(); ++v) {
+        const int id = pt_variant_by_name(t.variants[v].c_str());
+        if (id >= 0) reg_to_table[id] = (int)v;
+    }
+    clear_error();
+    auto time_of = [&](int id, int s) {
+        auto it = reg_to_table.find(id);
+        return it == reg_to_table.end() ? kInf : t.t[it->second][s];
+    };
+    const std::vector<double> tb = best_per_shape(t);
+    std::vector<int> shapes;
+    for (int i = 0; i < n; ++i) {
+        if (shape_idx[i] < 0 || shape_idx[i] >= (int)t.shapes.size())
+            return set_error(PT_EINVAL, 4, "shape index %d out of range", shape_idx[i]);
+        shapes.push_back(shape_idx[i]);
+    }
+    double total = 0;
+    if (mode == PT_SCORE_BEST_OF_SET) {
+        if (k < 1 || !ids) return set_error(PT_EINVAL, 2, "bad id list");
+        for (int s : shapes) {
+            double m = kInf;
+            for (int i = 0; i < k; ++i)
+                if (ids[i] >= 0) m = std::min(m, time_of(ids[i], s));
+            if (!std::isfinite(m)) {
+                *out_geomean = 0.0;
+                return PT_OK;
+            }
+            total += std::log(tb[s] / m);
+        }
+    } else if (mode == PT_SCORE_SELECTOR) {
+        if (!manifest_path) return set_error(PT_EINVAL, 7, "selector scoring needs a manifest");
+        Manifest m;
+        rc = read_manifest(manifest_path, &m);
+        if (rc != PT_OK) return rc;
+        for (int s : shapes) {
+            const int pick = manifest_pick(m, t.shapes[s]);
+            double tv = time_of(pick, s);
+            // Same fallback order as pt_sgemm: other members, then the default.
+            for (size_t i = 0; !std::isfinite(tv) && i < m.kappa.size(); ++i) tv = time_of(m.kappa[i], s);
+            if (!std::isfinite(tv)) tv = time_of(0, s);
+            if (!std::isfinite(tv)) {
+                *out_geomean = 0.0;
+                return PT_OK;
+            }
+            total += std::log(tb[s] / tv);
+        }
+    } else {
+        return set_error(PT_EINVAL, 6, "unknown scoring mode %d", mode);
+    }
+    *out_geomean = shapes.empty() ? 1.0 : std::exp(total / shapes.size());
+    return PT_OK;
+}
+
+}  // extern "C"

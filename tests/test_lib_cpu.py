@@ -1,0 +1,240 @@
+"""Host-side library checks (no GPU): the C ABI loads and exports every
+declared symbol, the registry follows the variant-space rules, and the C++
+selector / scorer / manifest agree with the oracle on synthetic tables."""
+
+import json
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import select as osel
+
+pt = pytest.importorskip("paper_2507_15277_gb300")
+from paper_2507_15277_gb300 import _lib  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pt_sgemm.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pt_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.SIGNATURES), "binding and header disagree"
+
+
+def test_registry_rules():
+    n = pt.num_variants()
+    assert 250 <= n <= 320
+    names = set()
+    for i in range(n):
+        d = pt.variant(i)
+        assert d["id"] == i
+        assert d["name"] not in names
+        names.add(d["name"])
+        assert d["bm"] % d["wm"] == 0 and d["bn"] % d["wn"] == 0
+        assert (d["wm"] // d["tm"]) * (d["wn"] // d["tn"]) * d["kl"] == 32
+        assert d["threads"] == 32 * (d["bm"] // d["wm"]) * (d["bn"] // d["wn"])
+        assert d["threads"] in (64, 128, 256, 512)
+        assert d["bk"] % (4 * d["kl"]) == 0
+        assert d["smem_bytes"] <= 232448
+        assert d["bm"] % d["splitk"] == 0
+        assert d["tm"] * d["tn"] <= 64
+        assert pt.variant_by_name(d["name"]) == i
+    d0 = pt.variant(pt.default_variant())
+    assert (d0["bm"], d0["bn"], d0["bk"], d0["vec"], d0["loader"], d0["trans_mask"]) == (128, 128, 8, 1, 0, 15)
+    for key, values in (("splitk", {1, 2, 4, 8}), ("loader", {0, 1}), ("vec", {1, 2, 4}),
+                        ("stages", {2, 3, 4}), ("bk", {8, 16, 32}), ("kl", {1, 2, 4})):
+        assert {pt.variant(i)[key] for i in range(n)} == values, key
+
+
+def test_argument_validation_without_gpu():
+    lib = _lib.lib()
+    rc = lib.pt_sgemm(b"X", b"N", 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None)
+    assert rc == _lib.PT_EINVAL and lib.pt_last_error_arg() == 1
+    rc = lib.pt_sgemm(b"N", b"N", -1, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None)
+    assert rc == _lib.PT_EINVAL and lib.pt_last_error_arg() == 3
+    rc = lib.pt_sgemm(b"N", b"N", 4, 4, 8, 1.0, None, 7, None, 4, 0.0, None, 4, None)
+    assert rc == _lib.PT_EINVAL and lib.pt_last_error_arg() == 8
+    rc = lib.pt_sgemm(b"N", b"T", 4, 4, 8, 1.0, None, 8, None, 4, 0.0, None, 4, None)
+    assert rc == _lib.PT_EINVAL and lib.pt_last_error_arg() == 10
+    rc = lib.pt_sgemm(b"N", b"N", 4, 5, 8, 1.0, None, 8, None, 5, 0.0, None, 4, None)
+    assert rc == _lib.PT_EINVAL and lib.pt_last_error_arg() == 13
+    # Empty output: nothing to do, no device touched.
+    assert lib.pt_sgemm(b"N", b"N", 0, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None) == 0
+    assert lib.pt_variant_desc(10 ** 6, None) == _lib.PT_EINVAL
+    assert lib.pt_variant_by_name(b"no_such_variant") == _lib.PT_EINVAL
+
+
+# ---- selection against the oracle ------------------------------------------------------
+
+HEADER_CSV = "shape_idx,M,N,K,transA,transB,variant,status,valid,median_ms,mean_ms,min_ms,reps,tflops,gbs,max_err"
+
+
+def write_table(path, times, shapes=None, names=None):
+    V, S = times.shape
+    names = names or [pt.variant(i)["name"] for i in range(V)]
+    shapes = shapes or [(64 * (s + 1), 128, 256, "N", "N") for s in range(S)]
+    with open(path, "w") as f:
+        f.write(HEADER_CSV + "\n")
+        for s in range(S):
+            for v in range(V):
+                t = times[v, s]
+                ok = np.isfinite(t)
+                m, n, k, ta, tb = shapes[s]
+                f.write("%d,%d,%d,%d,%s,%s,%s,%d,%d,%.17g,%.17g,%.17g,5,1,1,0\n" % (
+                    s, m, n, k, ta, tb, names[v], 0 if ok else -2, int(ok), t if ok else 0.0,
+                    t if ok else 0.0, t if ok else 0.0))
+    return names, shapes
+
+
+def random_table(seed, V, S, invalid=0.1):
+    rng = np.random.default_rng(seed)
+    t = np.exp(rng.normal(0, 0.6, size=(V, S)))
+    t[rng.random((V, S)) < invalid] = np.inf
+    for s in range(S):
+        if not np.isfinite(t[:, s]).any():
+            t[0, s] = 1.0
+    return t
+
+
+def test_golden_tiny_table(tmp_path):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "select_tiny.json")))
+    t = np.array(g["times"])
+    path = str(tmp_path / "t.csv")
+    write_table(path, t)
+    for k, opt in g["optimum"].items():
+        ids, val = pt.select(path, [0, 1, 2], int(k), method=pt.PT_SELECT_EXACT)
+        assert ids == opt["kappa"] and val == pytest.approx(opt["value"], rel=1e-12)
+        ids2, val2 = pt.select(path, [0, 1, 2], int(k), method=pt.PT_SELECT_GREEDY_SWAP)
+        assert val2 == pytest.approx(opt["value"], rel=1e-12), "swap search escapes the greedy trap"
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_exact_selection_matches_oracle(seed, tmp_path):
+    t = random_table(seed, 9, 7)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t)
+    train = [0, 2, 3, 5, 6] if seed % 2 else list(range(7))
+    for k in (1, 2, 3, 4):
+        ids, val = pt.select(path, train, k, method=pt.PT_SELECT_EXACT)
+        kappa, oval = osel.portability_tune_exhaustive(t, k, train)
+        assert val == pytest.approx(oval, rel=1e-12)
+        assert osel.set_performance(t, ids, train) == pytest.approx(oval, rel=1e-12)
+        assert ids == kappa
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_greedy_swap_quality(seed, tmp_path):
+    t = random_table(100 + seed, 14, 10, invalid=0.0)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t)
+    S = list(range(10))
+    for k in (2, 3, 4):
+        _, opt = osel.portability_tune_exhaustive(t, k, S)
+        ids, val = pt.select(path, S, k, method=pt.PT_SELECT_GREEDY_SWAP, seed=seed)
+        assert len(ids) == k
+        assert osel.set_performance(t, ids, S) == pytest.approx(val, rel=1e-12)
+        # facility-location bound on the shifted objective, and in practice near-optimal
+        lg = np.log(t.min(axis=0)[None, :] / t)
+        c = -lg.min()
+        f = lambda kap: float(np.sum(np.max(lg[list(kap)] + c, axis=0)))
+        kap_opt, _ = osel.portability_tune_exhaustive(t, k, S)
+        assert f(ids) >= (1 - 1 / math.e) * f(kap_opt) - 1e-9
+        assert val >= 0.97 * opt
+
+
+def test_score_best_of_set_and_selector(tmp_path):
+    t = random_table(7, 8, 12)
+    shapes = [(2 ** (6 + s % 4), 2 ** (6 + (s // 4) % 3), 2 ** (7 + s % 3), "N", "N") for s in range(12)]
+    shapes = list(dict.fromkeys(shapes))
+    t = t[:, :len(shapes)]
+    path = str(tmp_path / "t.csv")
+    names, _ = write_table(path, t, shapes=shapes)
+    S = len(shapes)
+    train = list(range(0, S, 2))
+    held = list(range(1, S, 2))
+    man = str(tmp_path / "m.json")
+    ids, val = pt.select(path, train, 3, method=pt.PT_SELECT_EXACT, manifest=man)
+    # best-of-set scoring == Eq. 1 on the held-out shapes
+    assert pt.score(path, held, ids) == pytest.approx(osel.set_performance(t, ids, held), rel=1e-12)
+    # selector-realised: each held-out shape takes its nearest training shape's pick
+    m = json.load(open(man))
+    assert [e["variant"] for e in m["map"]] == [names[osel.best_in_set(t, ids, s)] for s in train]
+    tb = osel.per_shape_best(t)
+    logs = []
+    map_shapes = [shapes[s] for s in train]
+    for s in held:
+        j = osel.nearest_shape(shapes[s][:3], [x[:3] for x in map_shapes])
+        v = osel.best_in_set(t, ids, train[j])
+        tv = t[v, s]
+        if not np.isfinite(tv):
+            fall = [t[i, s] for i in ids if np.isfinite(t[i, s])]
+            tv = fall[0] if fall else t[0, s]
+        logs.append(math.log(tb[s] / tv))
+    want = math.exp(sum(logs) / len(logs))
+    got = pt.score(path, held, mode=pt.PT_SCORE_SELECTOR, manifest=man)
+    assert got == pytest.approx(want, rel=1e-12)
+
+
+def test_manifest_round_trip_and_errors(tmp_path):
+    t = random_table(3, 5, 4, invalid=0.0)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t)
+    man = str(tmp_path / "m.json")
+    pt.select(path, [0, 1, 2, 3], 2, manifest=man)
+    pt.load_manifest(man)
+    pt.load_manifest(None)
+    bad = str(tmp_path / "bad.json")
+    open(bad, "w").write('{"format": "pt-manifest-1", "kappa": ["nope"]}')
+    with pytest.raises(pt.PtError) as e:
+        pt.load_manifest(bad)
+    assert e.value.code == _lib.PT_EFORMAT
+    open(bad, "w").write("{not json")
+    with pytest.raises(pt.PtError) as e:
+        pt.load_manifest(bad)
+    assert e.value.code == _lib.PT_EFORMAT
+    with pytest.raises(pt.PtError) as e:
+        pt.load_manifest(str(tmp_path / "missing.json"))
+    assert e.value.code == _lib.PT_EIO
+
+
+def test_malformed_and_truncated_tables(tmp_path):
+    t = random_table(4, 4, 3, invalid=0.0)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t)
+    lines = open(path).read().splitlines()
+    trunc = str(tmp_path / "trunc.csv")
+    open(trunc, "w").write("\n".join(lines[:-1]) + "\n" + lines[-1][:20] + "\n")
+    with pytest.raises(pt.PtError) as e:
+        pt.select(trunc, [0], 1)
+    assert e.value.code == _lib.PT_EFORMAT
+    hdr = str(tmp_path / "hdr.csv")
+    open(hdr, "w").write("a,b,c\n")
+    with pytest.raises(pt.PtError) as e:
+        pt.select(hdr, [0], 1)
+    assert e.value.code == _lib.PT_EFORMAT
+    # A later row for the same (shape, variant) replaces the earlier one (resume).
+    dup = str(tmp_path / "dup.csv")
+    name0 = pt.variant(0)["name"]
+    open(dup, "w").write("\n".join(lines) + "\n" + "0,64,128,256,N,N,%s,0,1,1e-9,1e-9,1e-9,5,1,1,0\n" % name0)
+    ids, val = pt.select(dup, [0], 1)
+    assert ids == [0]
+
+
+def test_table_shape_listing(tmp_path):
+    t = random_table(5, 3, 4, invalid=0.0)
+    path = str(tmp_path / "t.csv")
+    _, shapes = write_table(path, t)
+    assert pt.table_shapes(path) == shapes
