@@ -1,0 +1,422 @@
+"""Benchmark: portability-tuned SGEMM on the 64-shape sweep.
+
+One step = one pass of the hot path over the sweep workload: every
+(M, N, K) in {128, 512, 1024, 4096}^3 (FP32 row-major, alpha=1, beta=0,
+inputs U[-1,1] from SplitMix64 with seed 1000 + shape index) through the
+multi-versioned entry point pt_sgemm, whose runtime selector picks one of
+the k = 8 variants chosen by PortabilityTune on the training half of the
+shapes (the other half is held out).  Before the timed region the bench
+runs the data collection (timing table of every variant on every shape) and
+the selection (k = 1..8); their results are reported alongside.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Output: one JSON line on rank 0.  `value` is whole-job SGEMM TFLOP/s with
+inputs resident in HBM (1.6 GB of inputs, larger than L2); `e2e` adds the
+per-step host->device copies of A and B and the device->host copy of C.
+Multi-GPU: independent replicas (one per rank), weak scaling; no collective
+on the data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SGEMM TFLOP/s per shape; geomean % of per-shape best variant using k selected"
+UNIT = "TFLOP/s"
+WORKLOAD = "portability sweep: (M,N,K) in {128,512,1024,4096}^3, 64 shapes, FP32 row-major NN, alpha=1, beta=0, U[-1,1]"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--k", type=int, default=8, help="size of the deployed variant set")
+    p.add_argument("--table", default=None, help="reuse an existing timing table")
+    p.add_argument("--out-dir", default=None, help="where the table and manifests are written")
+    p.add_argument("--tune-reps-max", type=int, default=30)
+    p.add_argument("--tune-target-ms", type=float, default=3.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-rows", type=int, default=512, help="rows per shape in the CPU-oracle sample")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---- clocks ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_id
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- CPU oracle baseline -----------------------------------------------------------------
+def cpu_oracle_sample(shapes, rows_per_shape, seed_base=1000):
+    """Times the FP64 CPU oracle on the first `rows_per_shape` rows of every
+    shape (all rows when M is smaller).  Returns (TFLOP/s, seconds, cores, flops)."""
+    from oracle import gemm as og
+    from workloads import matrix
+    og.gemm(matrix("uniform", 0, 8, 8), matrix("uniform", 1, 8, 8))  # load / build the oracle
+    work = []
+    for i, (M, N, K) in enumerate(shapes):
+        r = min(M, rows_per_shape)
+        A = matrix("uniform", seed_base + i, r, K)  # the first r rows of A (same values)
+        B = matrix("uniform", 100000 + seed_base + i, K, N)
+        work.append((A, B, r, N, K))
+    flops = 0.0
+    t0 = time.perf_counter()
+    for A, B, r, N, K in work:
+        og.gemm(A, B)
+        flops += 2.0 * r * N * K
+    dt = time.perf_counter() - t0
+    return flops / dt / 1e12, dt, og.num_threads(), flops
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from workloads import sweep_shapes
+    shapes = sweep_shapes()
+    rows = max(1, args.cpu_rows // 4)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(shapes[:4], 8)
+    vals, secs, flops_total = [], 0.0, 0.0
+    cores = 1
+    for _ in range(args.steps):
+        v, dt, cores, fl = cpu_oracle_sample(shapes, rows)
+        vals.append(v)
+        secs += dt
+        flops_total += fl
+    value = flops_total / secs / 1e12
+    sample = "FP64 CPU oracle (i-k-j triple loop, OpenMP) on the first %d rows of each of the 64 sweep shapes per step" % rows
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---- our arm ----------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2507_15277_gb300 as pt
+    from workloads import matrix, parity_split, random_split, sweep_shapes
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    shapes = sweep_shapes()
+    train, held = parity_split()
+    out_dir = args.out_dir or tempfile.mkdtemp(prefix="ptbench_")
+    os.makedirs(out_dir, exist_ok=True)
+    table = args.table or os.path.join(out_dir, "table.csv")
+    info = {}
+
+    # ---- data collection + selection (rank 0; other ranks reuse its manifest) ----
+    if rank == 0:
+        t0 = time.perf_counter()
+        if not args.table:
+            pt.tune(shapes, table, reps_min=5, reps_max=args.tune_reps_max, target_ms=args.tune_target_ms)
+        info["tune_s"] = time.perf_counter() - t0
+        sel = {}
+        t0 = time.perf_counter()
+        for k in range(1, 9):
+            man = os.path.join(out_dir, "kappa_k%d.json" % k)
+            ids, g_train = pt.select(table, train, k, manifest=man)
+            sel[k] = {
+                "ids": ids,
+                "names": [pt.variant(i)["name"] for i in ids],
+                "train": g_train,
+                "heldout_best_of_set": pt.score(table, held, ids),
+                "heldout_selector": pt.score(table, held, mode=pt.PT_SCORE_SELECTOR, manifest=man),
+            }
+        info["select_s"] = time.perf_counter() - t0
+        # Mean and spread over 10 seeded random 32/32 splits.
+        rs = {}
+        for k in (1, 2, 4, 8):
+            vals = []
+            for seed in range(10):
+                tr, he = random_split(seed)
+                ids, _ = pt.select(table, tr, k)
+                vals.append(pt.score(table, he, ids))
+            rs[k] = (statistics.mean(vals), statistics.pstdev(vals))
+        info["random_splits"] = rs
+        info["selection"] = sel
+    barrier()
+    manifest = os.path.join(out_dir, "kappa_k%d.json" % args.k)
+    pt.load_manifest(manifest)
+
+    # ---- inputs: pinned host copies and resident device buffers ----
+    hostA, hostB, hostC, devA, devB, devC = [], [], [], [], [], []
+    flops = []
+    for i, (M, N, K) in enumerate(shapes):
+        a = torch.from_numpy(matrix("uniform", 1000 + i, M, K)).pin_memory()
+        b = torch.from_numpy(matrix("uniform", 100000 + 1000 + i, K, N)).pin_memory()
+        hostA.append(a)
+        hostB.append(b)
+        hostC.append(torch.empty((M, N), dtype=torch.float32).pin_memory())
+        devA.append(a.to(dev))
+        devB.append(b.to(dev))
+        devC.append(torch.empty((M, N), dtype=torch.float32, device=dev))
+        flops.append(2.0 * M * N * K)
+    step_flops = sum(flops)
+    picks = [pt.selected_variant(M, N, K, A=devA[i], B=devB[i], C=devC[i]) for i, (M, N, K) in enumerate(shapes)]
+    stream = torch.cuda.Stream(dev)
+
+    def step():
+        for i in range(len(shapes)):
+            pt.sgemm(devA[i], devB[i], devC[i], stream=stream)
+
+    # Capture the step once as a CUDA graph (64 launches, no host work).
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        step()  # warm (attribute setup, descriptors)
+        stream.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            step()
+    torch.cuda.synchronize()
+
+    # ---- per-shape times (events around each launch, same order) ----
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(shapes) + 1)]
+    per_shape = [[] for _ in shapes]
+    with torch.cuda.stream(stream):
+        for rep in range(3):
+            ev[0].record(stream)
+            for i in range(len(shapes)):
+                pt.sgemm(devA[i], devB[i], devC[i], stream=stream)
+                ev[i + 1].record(stream)
+            stream.synchronize()
+            for i in range(len(shapes)):
+                per_shape[i].append(ev[i].elapsed_time(ev[i + 1]))
+    shape_ms = [statistics.median(x) for x in per_shape]
+
+    # ---- timed region: graph replays ----
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.25)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+
+    # Eager (no graph) steps: the same launches issued from Python each step.
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1)
+
+    # ---- end to end: host inputs in, host result out, every step ----
+    h2d = sum(a.numel() * 4 + b.numel() * 4 for a, b in zip(hostA, hostB))
+    d2h = sum(c.numel() * 4 for c in hostC)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            for i in range(len(shapes)):
+                devA[i].copy_(hostA[i], non_blocking=True)
+                devB[i].copy_(hostB[i], non_blocking=True)
+                pt.sgemm(devA[i], devB[i], devC[i], stream=stream)
+                hostC[i].copy_(devC[i], non_blocking=True)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            for i in range(len(shapes)):
+                devA[i].copy_(hostA[i], non_blocking=True)
+                devB[i].copy_(hostB[i], non_blocking=True)
+                pt.sgemm(devA[i], devB[i], devC[i], stream=stream)
+                hostC[i].copy_(devC[i], non_blocking=True)
+        e1.record(stream)
+        stream.synchronize()
+        e2e_wall = time.perf_counter() - t0
+    e2e_ms = e0.elapsed_time(e1)
+
+    # Whole-job numbers: max time over ranks, units over all ranks.
+    t_local = torch.tensor([elapsed_ms, e2e_ms, eager_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    elapsed_ms, e2e_ms, eager_ms = [float(x) for x in t_local.tolist()]
+    value = world * step_flops * args.steps / (elapsed_ms * 1e-3) / 1e12
+    e2e_value = world * step_flops * args.steps / (e2e_ms * 1e-3) / 1e12
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel (largest share of the step) ----
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    dom = max(range(len(shapes)), key=lambda i: shape_ms[i])
+    M, N, K = shapes[dom]
+    dom_ms = shape_ms[dom]
+    achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
+    f_max = 2070.0
+    peak = sms * 128 * 2 * f_max * 1e6 / 1e12
+    f_med = clk.get("sm_mhz")
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        "traffic": None, "kernel": pt.variant(picks[dom])["name"], "shape": [M, N, K],
+        "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, f_max),
+        "frac_at_sampled_clock": (achieved / (sms * 256 * f_med * 1e6 / 1e12)) if f_med else None,
+        "share_of_step": dom_ms / sum(shape_ms),
+    }
+
+    # cuBLAS SGEMM (FP32, TF32 off) on the same shapes, as context.
+    torch.backends.cuda.matmul.allow_tf32 = False
+    torch.set_float32_matmul_precision("highest")
+    cub = []
+    with torch.cuda.stream(stream):
+        for i in range(len(shapes)):
+            torch.matmul(devA[i], devB[i], out=devC[i])
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            for i in range(len(shapes)):
+                torch.matmul(devA[i], devB[i], out=devC[i])
+        e1.record(stream)
+        stream.synchronize()
+    cublas_tflops = 3 * step_flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt, cores, fl = cpu_oracle_sample(shapes, args.cpu_rows)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 CPU oracle on the first %d rows of each of the 64 shapes (%.1f GFLOP, %.1f s)"
+                         % (args.cpu_rows, fl / 1e9, dt)}
+
+    sel = info.get("selection", {})
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shapes": 64, "k_deployed": args.k, "variants": pt.num_variants(),
+                   "train_split": "parity (i_m+i_n+i_k even) 32/32",
+                   "l2": "inputs 1.6 GB (> 129 MB L2) read once per step; no flush needed",
+                   "timed": "CUDA graph of the 64 pt_sgemm launches, replayed per step",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "clocks": clk,
+        "gpu_launches": 64 * args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "wall_s": e2e_wall},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "eager_value": world * step_flops * args.steps / (eager_ms * 1e-3) / 1e12,
+        "geomean_pct_of_best_heldout": {("k%d" % k): 100 * s["heldout_best_of_set"] for k, s in sel.items()},
+        "geomean_pct_of_best_heldout_selector": {("k%d" % k): 100 * s["heldout_selector"] for k, s in sel.items()},
+        "geomean_pct_of_best_train": {("k%d" % k): 100 * s["train"] for k, s in sel.items()},
+        "random_splits_heldout_pct": {("k%d" % k): [100 * m, 100 * sd] for k, (m, sd) in
+                                      info.get("random_splits", {}).items()},
+        "kappa": sel.get(args.k, {}).get("names"),
+        "tuning": {"tune_s": info.get("tune_s"), "select_s": info.get("select_s"), "table": table},
+        "per_shape": [{"shape": list(s), "ms": round(ms, 5), "tflops": round(f / (ms * 1e-3) / 1e12, 3),
+                       "variant": pt.variant(p)["name"]} for s, ms, f, p in zip(shapes, shape_ms, flops, picks)],
+        "context": {"cublas_sgemm_tflops": cublas_tflops, "fp32_peak_tflops_at_max_clock": peak, "sms": sms},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -15,7 +15,16 @@ and copied to the device.
 
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
+
+_PAR_MIN = 1 << 20
+
+
+def _workers():
+    return max(1, min(32, os.cpu_count() or 1))
 
 GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -42,32 +51,33 @@ def _bits(seed: int, n: int, offset: int = 0) -> np.ndarray:
     return splitmix64(seed, np.arange(offset, offset + n, dtype=np.uint64))
 
 
-def uniform_pm1(seed: int, n: int) -> np.ndarray:
+def uniform_pm1(seed: int, n: int, offset: int = 0) -> np.ndarray:
     """n FP32 values uniform on [-1, 1): 2*(x>>40)/2^24 - 1, exact in FP32."""
-    x = _bits(seed, n)
+    x = _bits(seed, n, offset)
     u = (x >> np.uint64(40)).astype(np.float64) * (2.0 ** -24)
     return (2.0 * u - 1.0).astype(np.float32)
 
 
-def small_ints(seed: int, n: int, lo: int = -8, hi: int = 8) -> np.ndarray:
+def small_ints(seed: int, n: int, offset: int = 0, lo: int = -8, hi: int = 8) -> np.ndarray:
     """n FP32 integers uniform on [lo, hi]."""
-    x = _bits(seed, n)
+    x = _bits(seed, n, offset)
     span = np.uint64(hi - lo + 1)
     return ((x >> np.uint64(32)) % span).astype(np.int64).astype(np.float32) + np.float32(lo)
 
 
-def normal(seed: int, n: int, std: float = 1.0) -> np.ndarray:
+def normal(seed: int, n: int, offset: int = 0, std: float = 1.0) -> np.ndarray:
     """n FP32 normals N(0, std^2): Box-Muller in FP64 on outputs 2i, 2i+1."""
-    x = _bits(seed, 2 * n)
+    x = _bits(seed, 2 * n, 2 * offset)
     u1 = ((x[0::2] >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
     u2 = (x[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
     z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
     return (z * std).astype(np.float32)
 
 
-def log_uniform_signed(seed: int, n: int, lo_exp: float = -10.0, hi_exp: float = 10.0) -> np.ndarray:
+def log_uniform_signed(seed: int, n: int, offset: int = 0, lo_exp: float = -10.0,
+                       hi_exp: float = 10.0) -> np.ndarray:
     """n FP32 values s * 2^e, s a random sign, e uniform on [lo_exp, hi_exp)."""
-    x = _bits(seed, n)
+    x = _bits(seed, n, offset)
     sign = np.where((x & np.uint64(1)) == 1, -1.0, 1.0)
     u = (x >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
     e = lo_exp + (hi_exp - lo_exp) * u
@@ -91,7 +101,20 @@ def matrix(kind: str, seed: int, rows: int, cols: int, ld: int | None = None, **
     ld = cols if ld is None else ld
     if ld < cols:
         raise ValueError("ld < cols")
-    vals = _KINDS[kind](seed, rows * cols, **kw).reshape(rows, cols) if rows * cols else np.zeros((rows, cols), np.float32)
+    n = rows * cols
+    fn = _KINDS[kind]
+    if n >= _PAR_MIN:
+        # Element i depends only on (seed, i): chunks are generated in parallel
+        # threads (numpy releases the GIL) and give the same values.
+        chunk = -(-n // _workers())
+        starts = list(range(0, n, chunk))
+        with ThreadPoolExecutor(max_workers=len(starts)) as ex:
+            parts = list(ex.map(lambda s0: fn(seed, min(chunk, n - s0), offset=s0, **kw), starts))
+        vals = np.concatenate(parts).reshape(rows, cols)
+    elif n:
+        vals = fn(seed, n, **kw).reshape(rows, cols)
+    else:
+        vals = np.zeros((rows, cols), np.float32)
     if ld == cols:
         return np.ascontiguousarray(vals)
     out = np.full((rows, ld), np.nan, dtype=np.float32)
