@@ -42,7 +42,7 @@ WORKLOAD = "portability sweep: (M,N,K) in {128,512,1024,4096}^3, 64 shapes, FP32
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--k", type=int, default=8, help="size of the deployed variant set")
@@ -52,7 +52,37 @@ def parse():
     p.add_argument("--tune-target-ms", type=float, default=3.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=512, help="rows per shape in the CPU-oracle sample")
+    p.add_argument("--single", default=None, metavar="M,N,K",
+                   help="profiling mode: run one variant (--variant) on one shape, no tuning")
+    p.add_argument("--variant", default=None, help="variant name for --single")
     return p.parse_args()
+
+
+def single(args):
+    """One variant on one shape, `warmup` + `steps` launches (for ncu captures)."""
+    import torch
+
+    import paper_2507_15277_gb300 as pt
+    from workloads import matrix
+    M, N, K = (int(x) for x in args.single.split(","))
+    vid = pt.variant_by_name(args.variant) if args.variant else pt.default_variant()
+    dev = torch.device("cuda", 0)
+    A = torch.from_numpy(matrix("uniform", 1, M, K)).to(dev)
+    B = torch.from_numpy(matrix("uniform", 2, K, N)).to(dev)
+    C = torch.empty((M, N), device=dev)
+    for _ in range(args.warmup):
+        pt.sgemm(A, B, C, variant=vid)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pt.sgemm(A, B, C, variant=vid)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"mode": "single", "variant": pt.variant(vid)["name"], "shape": [M, N, K], "ms": ms,
+                      "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12}))
+    return 0
 
 
 def dist_env():
@@ -168,6 +198,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.single:
+        return single(args)
 
     import numpy as np
     import torch

@@ -210,8 +210,11 @@ int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids, c
             ce = cudaMalloc(&buf.pool, want);
             if (ce != cudaSuccess) { rc = cuda_fail(ce, "pool allocation"); break; }
             buf.pool_bytes = want;
-            fill_uniform_kernel<<<4096, 256, 0, st>>>(reinterpret_cast<float *>(buf.pool), (int64_t)(want / 4), o.seed, 0);
         }
+        // Fresh U[-1,1) inputs for every shape: earlier shapes' outputs lie
+        // where this shape's A and B replicas are.
+        fill_uniform_kernel<<<4096, 256, 0, st>>>(reinterpret_cast<float *>(buf.pool), (int64_t)(buf.pool_bytes / 4),
+                                                  o.seed, 0);
         const int nrep = (int)std::max<size_t>(1, buf.pool_bytes / rep_bytes);
         auto A_of = [&](int r) { return reinterpret_cast<const float *>(buf.pool + (size_t)r * rep_bytes); };
         auto B_of = [&](int r) { return reinterpret_cast<const float *>(buf.pool + (size_t)r * rep_bytes + bA); };

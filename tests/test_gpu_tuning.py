@@ -37,7 +37,7 @@ def _times(rows, names, shapes):
 @pytest.fixture(scope="module")
 def small_table(tmp_path_factory):
     path = str(tmp_path_factory.mktemp("tune") / "table.csv")
-    shapes = [(128, 512, 1024), (512, 128, 128), (1024, 1024, 128), (256, 256, 2048)]
+    shapes = [(128, 512, 1024), (512, 128, 128), (1024, 1024, 128), (256, 256, 2048), (512, 512, 4096)]
     ids = list(range(0, pt.num_variants(), 9))
     pt.tune(shapes, path, ids=ids, reps_min=3, reps_max=10, target_ms=1.0)
     return path, shapes, ids
@@ -48,7 +48,9 @@ def test_table_rows_and_screening(small_table):
     rows = _read(path)
     assert len(rows) == len(shapes) * len(ids)
     valid = [r for r in rows if int(r["valid"])]
-    assert len(valid) >= 0.8 * len(rows)
+    for s in shapes:  # every shape, including those tuned after others, keeps valid rows
+        rs = [r for r in rows if (int(r["M"]), int(r["N"]), int(r["K"])) == s]
+        assert sum(int(r["valid"]) for r in rs) >= 0.8 * len(rs), s
     for r in valid:
         assert float(r["max_err"]) <= TOL_FP32
         assert float(r["median_ms"]) > 0 and float(r["tflops"]) > 0
@@ -76,7 +78,7 @@ def test_selection_on_measured_table_matches_oracle(small_table, tmp_path):
             names.append(r["variant"])
     keys = [s + ("N", "N") for s in shapes]
     t = _times(rows, names, keys)
-    train = [0, 1, 2, 3]
+    train = [0, 1, 2, 3, 4]
     for k in (1, 2, 3):
         got, g = pt.select(path, train, k, method=pt.PT_SELECT_EXACT)
         kappa, val = osel.portability_tune_exhaustive(t, k, train)
@@ -87,7 +89,7 @@ def test_selection_on_measured_table_matches_oracle(small_table, tmp_path):
 def test_manifest_drives_pt_sgemm(small_table, tmp_path):
     path, shapes, ids = small_table
     man = str(tmp_path / "kappa.json")
-    got, g = pt.select(path, [0, 1, 2, 3], 2, manifest=man)
+    got, g = pt.select(path, [0, 1, 2, 3, 4], 2, manifest=man)
     pt.load_manifest(man)
     try:
         rows = _read(path)
