@@ -98,6 +98,7 @@ typedef struct pt_variant_desc {
     int trans_mask;    /* bit (2*tA + tB) set when (transA, transB) runs;
                           tX = 0 for 'N', 1 for 'T'                          */
     int kind;          /* 0 = FP32 SIMT                                      */
+    int fma2;          /* 1: packed fma.rn.f32x2 register-tile updates       */
     char name[96];     /* stable key used in tables and manifests           */
 } pt_variant_desc_t;
 

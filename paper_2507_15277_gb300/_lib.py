@@ -38,7 +38,7 @@ _p = ctypes.c_void_p
 class VariantDesc(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in (
         "id", "bm", "bn", "bk", "wm", "wn", "tm", "tn", "kl", "vec", "stages", "splitk", "loader",
-        "a_kmajor", "threads", "smem_bytes", "trans_mask", "kind")] + [("name", ctypes.c_char * 96)]
+        "a_kmajor", "threads", "smem_bytes", "trans_mask", "kind", "fma2")] + [("name", ctypes.c_char * 96)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_ if n != "name"}

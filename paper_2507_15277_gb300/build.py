@@ -84,7 +84,7 @@ def _compile(args):
     return src, ("\n".join(spills) if spills else None)
 
 
-_SIMT_ARGS = re.compile(r"SimtI((?:Li-?\d+E){13})E")
+_SIMT_ARGS = re.compile(r"SimtI((?:Li-?\d+E){14})E")
 
 
 def _spilled_variants(objs, fam):

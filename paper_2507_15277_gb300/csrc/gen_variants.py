@@ -7,6 +7,7 @@ The variant space is the Cartesian grid of tuning parameters
     vector width VEC in {1, 2, 4}              pipeline depth STAGES in {2, 3, 4}
     cluster split-K SPLITK in {1, 2, 4, 8}     staging: cp.async with M-major A,
                                                cp.async with K-major A, TMA with K-major A
+    FMA form F2 in {0: fmaf, 1: packed fma.rn.f32x2}
 
 pruned by static validity rules (threads per CTA in {64, 128, 256, 512},
 lane layout that tiles the warp, BK a multiple of 4*KL, shared memory within
@@ -15,7 +16,7 @@ SPLITK, register tile at most 64 accumulators).  Like the paper's dataset
 (a hand-tuned subset followed by a random selection from the kernel space,
 Section V-D), the compiled family is a fixed core of conventional
 configurations plus a SplitMix64-seeded stratified sample of the rest, about
-300 variants in total.  Output: ``variant_table.inc`` (every variant as an
+380 variants in total.  Output: ``variant_table.inc`` (every variant as an
 X-macro row) and ``variants_XX.cu`` translation units that instantiate them,
 compiled in parallel.
 """
@@ -27,7 +28,7 @@ import math
 import os
 import sys
 
-TARGET_COUNT = 300
+TARGET_COUNT = 384
 SAMPLE_SEED = 20250715
 N_TUS = 24
 SMEM_LIMIT = 232448
@@ -83,7 +84,7 @@ def smem_bytes(BM, BN, BK, STAGES, SPLITK, LOADER, AKM):
 
 def name_of(v):
     return ("s{BM}x{BN}x{BK}_w{WM}x{WN}_t{TM}x{TN}_kl{KL}_v{VEC}_p{STAGES}_sk{SPLITK}_{fam}"
-            .format(**v))
+            .format(**v)) + ("_ffma2" if v.get("F2") else "")
 
 
 def enumerate_space():
@@ -111,11 +112,12 @@ def enumerate_space():
                                     sm = smem_bytes(BM, BN, BK, STAGES, SPLITK, LOADER, AKM)
                                     if sm > SMEM_LIMIT:
                                         continue
-                                    v = dict(BM=BM, BN=BN, BK=BK, WM=WM, WN=WN, TM=TM, TN=TN, KL=KL, VEC=VEC,
-                                             STAGES=STAGES, SPLITK=SPLITK, LOADER=LOADER, AKM=AKM, fam=fam,
-                                             threads=threads, smem=sm)
-                                    v["name"] = name_of(v)
-                                    out.append(v)
+                                    for F2 in (0, 1):
+                                        v = dict(BM=BM, BN=BN, BK=BK, WM=WM, WN=WN, TM=TM, TN=TN, KL=KL,
+                                                 VEC=VEC, STAGES=STAGES, SPLITK=SPLITK, LOADER=LOADER, AKM=AKM,
+                                                 F2=F2, fam=fam, threads=threads, smem=sm)
+                                        v["name"] = name_of(v)
+                                        out.append(v)
     return out
 
 
@@ -137,11 +139,12 @@ def core_set(space):
             for BK in (8, 16):
                 for STAGES in (2, 3, 4):
                     for SPLITK in (1, 4) if BM * BN <= 128 * 128 else (1,):
-                        v = dict(BM=BM, BN=BN, BK=BK, WM=WM, WN=WN, TM=TM, TN=TN, KL=KL, VEC=4,
-                                 STAGES=STAGES, SPLITK=SPLITK, fam=fam)
-                        n = name_of(v)
-                        if n in by_name and (STAGES == 3 or SPLITK == 1 and BK == 8):
-                            want.append(n)
+                        for F2 in (0, 1):
+                            v = dict(BM=BM, BN=BN, BK=BK, WM=WM, WN=WN, TM=TM, TN=TN, KL=KL, VEC=4,
+                                     STAGES=STAGES, SPLITK=SPLITK, fam=fam, F2=F2)
+                            n = name_of(v)
+                            if n in by_name and (STAGES == 3 or SPLITK == 1 and BK == 8):
+                                want.append(n)
     seen, out = set(), []
     for n in want:
         if n not in seen:
@@ -187,7 +190,7 @@ def build_family():
     # The default variant (128x128x8, 8x8 threads, cp.async M-major A, VEC=1,
     # 2 stages, no split) runs every layout and alignment; it is always id 0.
     default = dict(BM=128, BN=128, BK=8, WM=32, WN=64, TM=8, TN=8, KL=1, VEC=1, STAGES=2, SPLITK=1,
-                   LOADER=0, AKM=0, fam="cpm")
+                   LOADER=0, AKM=0, F2=0, fam="cpm")
     lay = lane_layout(128, 128, 8, 8, 1)
     default["WM"], default["WN"] = lay[0] * 8, lay[1] * 8
     default["name"] = name_of(default)
@@ -195,7 +198,7 @@ def build_family():
     return fam, len(space)
 
 
-PARAM_ORDER = ("BM", "BN", "BK", "WM", "WN", "TM", "TN", "KL", "VEC", "STAGES", "SPLITK", "LOADER", "AKM")
+PARAM_ORDER = ("BM", "BN", "BK", "WM", "WN", "TM", "TN", "KL", "VEC", "STAGES", "SPLITK", "LOADER", "AKM", "F2")
 
 
 def params_of(v):

@@ -27,6 +27,7 @@ pt_variant_desc_t make_desc(int id, const char *name) {
     if (V::LOADER == kLoaderTma) d.trans_mask = V::AKM ? 1 /* NN */ : 4 /* TN */;
     else d.trans_mask = V::AKM ? (1 | 2) /* NN, NT */ : 15;
     d.kind = 0;
+    d.fma2 = V::F2;
     std::strncpy(d.name, name, sizeof(d.name) - 1);
     return d;
 }

@@ -19,6 +19,9 @@
 //             cluster-rank order (deterministic, no atomics, no workspace)
 //   LOADER    0: cp.async (LDGSTS) staging by all threads
 //             1: TMA (cp.async.bulk.tensor) issued by one thread, mbarrier
+//   F2        1: the register tile is updated with packed fma.rn.f32x2 (two
+//             FP32 FMAs per instruction, same IEEE results), halving FMA issue
+//             slots; 0: one fmaf per product
 //   AKM       1: the A tile is held K-major in shared memory (rows of BK
 //             floats, XOR-swizzled in 16-byte units with the TMA swizzle of
 //             span BK*4 bytes) and read four k at a time; 0: held M-major
@@ -69,11 +72,11 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
 
 template <int BM_, int BN_, int BK_, int WM_, int WN_, int TM_, int TN_, int KL_, int VEC_, int STAGES_,
-          int SPLITK_, int LOADER_, int AKM_>
+          int SPLITK_, int LOADER_, int AKM_, int F2_ = 0>
 struct Simt {
     static constexpr int BM = BM_, BN = BN_, BK = BK_, WM = WM_, WN = WN_, TM = TM_, TN = TN_;
     static constexpr int KL = KL_, VEC = VEC_, STAGES = STAGES_, SPLITK = SPLITK_;
-    static constexpr int LOADER = LOADER_, AKM = AKM_;
+    static constexpr int LOADER = LOADER_, AKM = AKM_, F2 = F2_;
 
     static constexpr int WARPS_M = BM / WM, WARPS_N = BN / WN;
     static constexpr int WARPS = WARPS_M * WARPS_N;
@@ -111,6 +114,21 @@ struct Simt {
     static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
     static_assert(THREADS <= 1024, "threads");
 };
+
+// ---- packed FP32x2 FMA (sm_100+): two IEEE fused multiply-adds per instruction
+__device__ __forceinline__ uint64_t pack2(float x, float y) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(uint64_t v, float &x, float &y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+}
+
+__device__ __forceinline__ void fma2(uint64_t &d, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
 
 // ---- global -> shared copies (cp.async) ------------------------------------
 
@@ -248,6 +266,14 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+    // Packed accumulators for the FP32x2 path: acc2[i][p] holds columns 2p, 2p+1.
+    uint64_t acc2[V::F2 ? TM : 1][V::F2 ? TN / 2 : 1];
+    if constexpr (V::F2) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int p = 0; p < TN / 2; ++p) acc2[i][p] = 0ull;
+    }
 
     auto load_stage = [&](int s, int kt) {
         const int k0 = kt * BK;
@@ -304,7 +330,7 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const int k = t * KL * 4 + kk;  // this k-group's k is k + 4*g (folded into offsets)
-                float a[TM], b[TN];
+                float a[TM], b[V::F2 ? 1 : TN];
                 if constexpr (AKM) {
 #pragma unroll
                     for (int i = 0; i < TM; ++i) a[i] = a4[i][kk];
@@ -315,15 +341,32 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
                         a[4 * c] = v.x; a[4 * c + 1] = v.y; a[4 * c + 2] = v.z; a[4 * c + 3] = v.w;
                     }
                 }
+                if constexpr (V::F2) {
+                    uint64_t b2[TN / 2];
 #pragma unroll
-                for (int c = 0; c < TN / 4; ++c) {
-                    const float4 v = *reinterpret_cast<const float4 *>(pB + b_off + (k * V::B_LD + c * 4 * LN) * 4);
-                    b[4 * c] = v.x; b[4 * c + 1] = v.y; b[4 * c + 2] = v.z; b[4 * c + 3] = v.w;
+                    for (int c = 0; c < TN / 4; ++c) {
+                        const ulonglong2 v =
+                            *reinterpret_cast<const ulonglong2 *>(pB + b_off + (k * V::B_LD + c * 4 * LN) * 4);
+                        b2[2 * c] = v.x;
+                        b2[2 * c + 1] = v.y;
+                    }
+#pragma unroll
+                    for (int i = 0; i < TM; ++i) {
+                        const uint64_t ad = pack2(a[i], a[i]);
+#pragma unroll
+                        for (int p = 0; p < TN / 2; ++p) fma2(acc2[i][p], ad, b2[p]);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < TN / 4; ++c) {
+                        const float4 v = *reinterpret_cast<const float4 *>(pB + b_off + (k * V::B_LD + c * 4 * LN) * 4);
+                        b[4 * c] = v.x; b[4 * c + 1] = v.y; b[4 * c + 2] = v.z; b[4 * c + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
                 }
-#pragma unroll
-                for (int i = 0; i < TM; ++i)
-#pragma unroll
-                    for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
             }
         }
     };
@@ -386,6 +429,13 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
         }
         cp_async_wait<0>();
         __syncthreads();
+    }
+
+    if constexpr (V::F2) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int p = 0; p < TN / 2; ++p) unpack2(acc2[i][p], acc[i][2 * p], acc[i][2 * p + 1]);
     }
 
     // Combine the k-groups of each warp (butterfly; every group ends with the

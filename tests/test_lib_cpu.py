@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_registry_rules():
     n = pt.num_variants()
-    assert 250 <= n <= 320
+    assert 300 <= n <= 400
     names = set()
     for i in range(n):
         d = pt.variant(i)
@@ -55,7 +55,7 @@ def test_registry_rules():
     d0 = pt.variant(pt.default_variant())
     assert (d0["bm"], d0["bn"], d0["bk"], d0["vec"], d0["loader"], d0["trans_mask"]) == (128, 128, 8, 1, 0, 15)
     for key, values in (("splitk", {1, 2, 4, 8}), ("loader", {0, 1}), ("vec", {1, 2, 4}),
-                        ("stages", {2, 3, 4}), ("bk", {8, 16, 32}), ("kl", {1, 2, 4})):
+                        ("stages", {2, 3, 4}), ("bk", {8, 16, 32}), ("kl", {1, 2, 4}), ("fma2", {0, 1})):
         assert {pt.variant(i)[key] for i in range(n)} == values, key
 
 
