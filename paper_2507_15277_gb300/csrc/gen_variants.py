@@ -78,7 +78,7 @@ def smem_bytes(BM, BN, BK, STAGES, SPLITK, LOADER, AKM):
     b_stage = round_up(BK * (BN + pad) * 4, 1024)
     pipe = STAGES * (a_stage + b_stage)
     red = BM * (BN + 4) * 4 if SPLITK > 1 else 0
-    bars = 8 * STAGES if LOADER == 1 else 0
+    bars = 16 * STAGES if LOADER == 1 else 0
     return max(pipe, red) + bars + 1024
 
 

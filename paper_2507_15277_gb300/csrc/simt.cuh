@@ -92,7 +92,7 @@ struct Simt {
     static constexpr int RED_LD = BN + 4;
     static constexpr int RED_BYTES = SPLITK > 1 ? BM * RED_LD * 4 : 0;
     static constexpr int BAR_OFFSET = cmax(PIPE_BYTES, RED_BYTES);
-    static constexpr int BAR_BYTES = LOADER == kLoaderTma ? 8 * STAGES : 0;
+    static constexpr int BAR_BYTES = LOADER == kLoaderTma ? 16 * STAGES : 0;
     static constexpr int ALIGN_SLACK = 1024;
     static constexpr int SMEM_BYTES = BAR_OFFSET + BAR_BYTES + ALIGN_SLACK;
     // XOR swizzle of the K-major A tile: 16-byte unit index ^= (byte >> 7) & SW_MASK
@@ -373,42 +373,61 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
 
     bool failed = false;
     if constexpr (TMA) {
+        // full[s] (bar0 + 8s): completes when stage s's TMA bytes have landed
+        // (one arrive: the producer's expect_tx).  empty[s] (emp0 + 8s):
+        // completes when every warp has finished reading stage s (one arrive
+        // per warp).  Warps never wait for each other: the producer thread
+        // refills the stage read one iteration earlier, so its empty wait is
+        // normally already satisfied.
+        const uint32_t emp0 = bar0 + 8 * STAGES;
         if (tid == 0) {
             prefetch_tensormap(&tmA);
             prefetch_tensormap(&tmB);
 #pragma unroll
-            for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
+            for (int s = 0; s < STAGES; ++s) {
+                mbar_init(bar0 + 8 * s, 1);
+                mbar_init(emp0 + 8 * s, V::WARPS);
+            }
             fence_mbarrier_init();
         }
         __syncthreads();
-        int issued = 0;
+        const int pre = STAGES < nkt ? STAGES : nkt;
+        int issued = 0, seen = 0;  // k-tiles issued / waited on (thread 0's view)
         if (tid == 0) {
-            for (int s = 0; s < STAGES - 1 && s < nkt; ++s) load_stage(s, kt_begin + s);
+            for (int s = 0; s < pre; ++s) load_stage(s, kt_begin + s);
+            issued = pre;
         }
-        issued = (STAGES - 1 < nkt) ? STAGES - 1 : nkt;
+        bool ok = true;
         int s = 0;
         uint32_t phase = 0;
-        int it = 0;
-        for (; it < nkt; ++it) {
-            const bool ok = mbar_wait_bounded(bar0 + 8 * s, phase, kWaitLimitNs);
-            if (__syncthreads_or(!ok)) {
-                failed = true;
+        for (int it = 0; it < nkt; ++it) {
+            if (!mbar_wait_bounded(bar0 + 8 * s, phase, kWaitLimitNs)) {
+                ok = false;
                 break;
             }
-            const int nx = it + STAGES - 1;
-            if (nx < nkt) {
-                const int sn = (s + STAGES - 1) % STAGES;
-                if (tid == 0) load_stage(sn, kt_begin + nx);
-                ++issued;
-            }
+            seen = it + 1;
             compute_stage(s);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(emp0 + 8 * s);
+            const int j = it - 1 + STAGES;  // refill the stage read at it - 1 with k-tile j
+            if (tid == 0 && it >= 1 && j < nkt) {
+                const int sp = (s + STAGES - 1) % STAGES;
+                if (!mbar_wait_bounded(emp0 + 8 * sp, (uint32_t)(((it - 1) / STAGES) & 1), kWaitLimitNs)) {
+                    ok = false;
+                    break;
+                }
+                load_stage(sp, kt_begin + j);
+                issued = j + 1;
+            }
             if (++s == STAGES) { s = 0; phase ^= 1u; }
         }
-        if (failed) {
-            if (tid == 0 && args.err) atomicOr(args.err, 1);
-            // Let every TMA copy still in flight land before the CTA exits.
-            for (int j = it; j < issued; ++j)
-                (void)mbar_wait_bounded(bar0 + 8 * (j % STAGES), (uint32_t)((j / STAGES) & 1), kWaitLimitNs);
+        failed = __syncthreads_or(!ok);
+        if (failed && tid == 0) {
+            if (args.err) atomicOr(args.err, 1);
+            // Let every TMA copy still in flight land before shared memory is
+            // reused or the CTA exits.
+            for (int q = seen; q < issued; ++q)
+                (void)mbar_wait_bounded(bar0 + 8 * (q % STAGES), (uint32_t)((q / STAGES) & 1), kWaitLimitNs);
         }
         __syncthreads();
     } else {
