@@ -97,7 +97,8 @@ typedef struct pt_variant_desc {
     int smem_bytes;    /* dynamic shared memory per CTA                      */
     int trans_mask;    /* bit (2*tA + tB) set when (transA, transB) runs;
                           tX = 0 for 'N', 1 for 'T'                          */
-    int kind;          /* 0 = FP32 SIMT                                      */
+    int kind;          /* 0 = FP32 SIMT, 1 = 3xTF32 tensor core (tcgen05),
+                          2 = BF16x3 tensor core (tcgen05, six products)     */
     int fma2;          /* 1: packed fma.rn.f32x2 register-tile updates       */
     char name[96];     /* stable key used in tables and manifests           */
 } pt_variant_desc_t;
@@ -106,6 +107,12 @@ int pt_num_variants(void);
 int pt_variant_desc(int id, pt_variant_desc_t *out);
 /* id of a variant by name, or PT_EINVAL */
 int pt_variant_by_name(const char *name);
+/* The split-precision tensor-core variants (kind 1, 2) split both operands
+ * into low-precision planes in a library workspace (see pt_shutdown) and run
+ * tcgen05.mma with TMEM accumulators; they accept every layout and alignment.
+ * 3xTF32 (Markidis et al.-style split x = hi + lo, three products) and BF16x3
+ * (x = b0 + b1 + b2, six products) give FP32-level error.  The paper has no
+ * tensor-core versions; they are further members of the same variant space. */
 /* the fixed default variant (128x128x8 CTA tile, cp.async, any layout) */
 int pt_default_variant(void);
 
@@ -179,6 +186,13 @@ int pt_load_manifest(const char *path);
 int pt_selected_variant(char transA, char transB, int64_t M, int64_t N, int64_t K,
                         const float *A, int64_t lda, const float *B, int64_t ldb,
                         const float *C, int64_t ldc);
+
+/* Frees the library's device workspaces (the split planes of the tensor-core
+ * variants, one buffer per device and stream, grown on first use of a larger
+ * shape; growing is refused with PT_EUNSUPPORTED while the stream is being
+ * captured, and pt_sgemm then falls back to another variant) and unloads the
+ * manifest.  Synchronises the devices that hold a workspace. */
+int pt_shutdown(void);
 
 /* Device-side error word set by kernels whose bounded waits gave up
  * (PT_ETIMEOUT) on the current device; reading clears it.  Synchronises the

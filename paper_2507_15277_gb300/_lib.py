@@ -85,6 +85,7 @@ SIGNATURES = {
     "pt_selected_variant": (ctypes.c_int, [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _p, _i64, _p, _i64,
                                            _p, _i64]),
     "pt_device_status": (ctypes.c_int, []),
+    "pt_shutdown": (ctypes.c_int, []),
 }
 
 _lib = None

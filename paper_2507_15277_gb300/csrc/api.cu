@@ -14,6 +14,8 @@
 
 namespace pt {
 
+void free_workspaces();  // tc.cu
+
 // ---- errors ---------------------------------------------------------------------
 static thread_local char g_msg[512];
 static thread_local int g_arg = 0;
@@ -300,6 +302,14 @@ int pt_device_status(void) {
         cudaMemcpyToSymbol(g_err_word, &zero, sizeof(int));
         return set_error(PT_ETIMEOUT, 0, "a bounded device wait gave up (word %d)", v);
     }
+    return PT_OK;
+}
+
+int pt_shutdown(void) {
+    clear_error();
+    free_workspaces();
+    std::lock_guard<std::mutex> lk(g_manifest_mu);
+    g_manifest.reset();
     return PT_OK;
 }
 

@@ -2,6 +2,8 @@
 // (descriptor + launcher), in the order written by gen_variants.py, minus
 // the variants whose compilation spilled registers (dropped by the build).
 #include <cstring>
+#include <iterator>
+#include <vector>
 
 #include "launch.cuh"
 
@@ -40,7 +42,22 @@ const VariantEntry kTable[] = {
 
 }  // namespace
 
-const VariantEntry *variant_table() { return kTable; }
-int variant_table_size() { return (int)(sizeof(kTable) / sizeof(kTable[0])); }
+std::vector<VariantEntry> tc_variants();  // tc.cu
+
+// SIMT family first (id 0 is the default variant), tensor-core variants after.
+const std::vector<VariantEntry> &all_variants() {
+    static const std::vector<VariantEntry> v = [] {
+        std::vector<VariantEntry> out(std::begin(kTable), std::end(kTable));
+        for (VariantEntry e : tc_variants()) {
+            e.desc.id = (int)out.size();
+            out.push_back(e);
+        }
+        return out;
+    }();
+    return v;
+}
+
+const VariantEntry *variant_table() { return all_variants().data(); }
+int variant_table_size() { return (int)all_variants().size(); }
 
 }  // namespace pt

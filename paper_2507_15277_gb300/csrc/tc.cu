@@ -1,0 +1,178 @@
+// Host side of the split-precision tensor-core variants: workspace for the
+// split planes, tensor maps, launches, registry entries.
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "launch.cuh"
+#include "tc.cuh"
+
+namespace pt {
+namespace {
+
+// ---- workspace: one buffer per (device, stream), grown on demand ----------------
+std::mutex g_ws_mu;
+std::map<std::pair<int, uintptr_t>, std::pair<void *, size_t>> g_ws;
+
+int workspace(cudaStream_t st, size_t need, bool dry, void **out) {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    auto &e = g_ws[{dev, reinterpret_cast<uintptr_t>(st)}];
+    if (e.second >= need) {
+        *out = e.first;
+        return PT_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(PT_EUNSUPPORTED, 0, "cannot query the stream's capture state");
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+        return set_error(PT_EUNSUPPORTED, 0, "split workspace must grow while the stream is being captured");
+    if (dry) return PT_OK;
+    if (e.first) {
+        cudaStreamSynchronize(st);
+        cudaFree(e.first);
+        e = {nullptr, 0};
+    }
+    size_t bytes = need + need / 4;
+    bytes = (bytes + ((size_t)2 << 20) - 1) & ~(((size_t)2 << 20) - 1);
+    void *p = nullptr;
+    cudaError_t err = cudaMalloc(&p, bytes);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(PT_ECUDA, 0, "workspace allocation of %zu bytes: %s", bytes, cudaGetErrorString(err));
+    }
+    e = {p, bytes};
+    *out = p;
+    return PT_OK;
+}
+
+int make_map_3d(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int elem, int64_t inner, int64_t rows,
+                int64_t planes, int64_t pitch_bytes, int64_t plane_bytes, int box_inner, int box_rows) {
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return set_error(PT_ECUDA, 0, "cuTensorMapEncodeTiled unavailable");
+    (void)elem;
+    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch_bytes, (cuuint64_t)plane_bytes};
+    cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(PT_ECUDA, 0, "cuTensorMapEncodeTiled (3-D) failed (%d)", (int)r);
+    return PT_OK;
+}
+
+inline int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
+
+template <class V>
+int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
+    const int64_t gy = ((int64_t)a.M + V::BM - 1) / V::BM;
+    if (gy > 65535 || ((int64_t)a.M + 31) / 32 > 65535 || ((int64_t)a.N + 31) / 32 > 65535)
+        return set_error(PT_EUNSUPPORTED, 3, "shape too large for this variant's grid");
+    const int64_t pitch = ((int64_t)a.K + (16 / V::ELEM) - 1) / (16 / V::ELEM) * (16 / V::ELEM);
+    const int64_t a_plane = align256((int64_t)a.M * pitch * V::ELEM);
+    const int64_t b_plane = align256((int64_t)a.N * pitch * V::ELEM);
+    const size_t need = (size_t)V::P * (size_t)(a_plane + b_plane);
+    void *ws = nullptr;
+    int rc = workspace(st, need, dry, &ws);
+    if (rc != PT_OK || dry) return rc;
+
+    static std::atomic<uint64_t> attr_done{0};
+    const int dev = current_device();
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(attr_done.load(std::memory_order_acquire) & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(tc_sgemm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             V::SMEM_BYTES);
+        if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        attr_done.fetch_or(bit, std::memory_order_acq_rel);
+    }
+
+    unsigned char *wA = static_cast<unsigned char *>(ws);
+    unsigned char *wB = wA + V::P * a_plane;
+    const dim3 blk(32, 8);
+    tc_split_kernel<V::KIND><<<dim3((unsigned)((a.K + 31) / 32), (unsigned)((a.M + 31) / 32)), blk, 0, st>>>(
+        a.A, a.lda, a.ta, a.M, a.K, wA, a_plane, pitch);
+    tc_split_kernel<V::KIND><<<dim3((unsigned)((a.K + 31) / 32), (unsigned)((a.N + 31) / 32)), blk, 0, st>>>(
+        a.B, a.ldb, a.tb ? 0 : 1, a.N, a.K, wB, b_plane, pitch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
+
+    const CUtensorMapDataType dt =
+        V::KIND == kTcTf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUtensorMap mA, mB;
+    rc = make_map_3d(&mA, wA, dt, V::ELEM, a.K, a.M, V::P, pitch * V::ELEM, a_plane, V::BK, V::BM);
+    if (rc != PT_OK) return rc;
+    rc = make_map_3d(&mB, wB, dt, V::ELEM, a.K, a.N, V::P, pitch * V::ELEM, b_plane, V::BK, V::BN);
+    if (rc != PT_OK) return rc;
+
+    TcArgs t;
+    t.C = a.C;
+    t.ldc = a.ldc;
+    t.M = a.M;
+    t.N = a.N;
+    t.K = a.K;
+    t.alpha = a.alpha;
+    t.beta = a.beta;
+    t.vec4 = (!misaligned(a.C, 16) && a.ldc % 4 == 0) ? 1 : 0;
+    t.err = a.err;
+    const dim3 grid((unsigned)((a.N + V::BN - 1) / V::BN), (unsigned)gy);
+    tc_sgemm_kernel<V><<<grid, V::THREADS, V::SMEM_BYTES, st>>>(t, mA, mB);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "tensor-core kernel: %s", cudaGetErrorString(e));
+    return PT_OK;
+}
+
+template <class V>
+VariantEntry tc_entry(const char *name) {
+    VariantEntry v;
+    std::memset(&v.desc, 0, sizeof(v.desc));
+    v.desc.bm = V::BM;
+    v.desc.bn = V::BN;
+    v.desc.bk = V::BK;
+    v.desc.kl = 1;
+    v.desc.vec = 1;
+    v.desc.stages = V::STAGES;
+    v.desc.splitk = 1;
+    v.desc.loader = PT_LOADER_TMA;
+    v.desc.a_kmajor = 1;
+    v.desc.threads = V::THREADS;
+    v.desc.smem_bytes = V::SMEM_BYTES;
+    v.desc.trans_mask = 15;
+    v.desc.kind = V::KIND == kTcTf32 ? 1 : 2;
+    std::strncpy(v.desc.name, name, sizeof(v.desc.name) - 1);
+    v.launch = launch_tc<V>;
+    return v;
+}
+
+}  // namespace
+
+// Tensor-core variants appended to the registry after the SIMT family.
+std::vector<VariantEntry> tc_variants() {
+    return {
+        tc_entry<Tc<kTcTf32, 256, 2>>("tc3xtf32_m128n256_p2"),
+        tc_entry<Tc<kTcTf32, 128, 3>>("tc3xtf32_m128n128_p3"),
+        tc_entry<Tc<kTcTf32, 64, 4>>("tc3xtf32_m128n64_p4"),
+        tc_entry<Tc<kTcBf16x3, 128, 2>>("tcbf16x3_m128n128_p2"),
+        tc_entry<Tc<kTcBf16x3, 64, 3>>("tcbf16x3_m128n64_p3"),
+    };
+}
+
+void free_workspaces() {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    for (auto &kv : g_ws) {
+        if (kv.second.first) {
+            int cur = 0;
+            cudaGetDevice(&cur);
+            cudaSetDevice(kv.first.first);
+            cudaDeviceSynchronize();
+            cudaFree(kv.second.first);
+            cudaSetDevice(cur);
+        }
+    }
+    g_ws.clear();
+}
+
+}  // namespace pt

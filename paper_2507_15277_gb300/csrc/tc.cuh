@@ -1,0 +1,314 @@
+// Split-precision tensor-core SGEMM variants for sm_103a (tcgen05 + TMEM + TMA).
+//
+// FP32 operands are split into low-precision planes whose products the 5th-
+// generation tensor cores compute exactly and accumulate in FP32 in tensor
+// memory:
+//   3xTF32:  x = hi + lo, hi = RN_tf32(x), lo = RN_tf32(x - hi);
+//            a*b ~ hi_a*hi_b + hi_a*lo_b + lo_a*hi_b      (kind::tf32, 3 MMAs)
+//   BF16x3:  x = b0 + b1 + b2, b0 = RN_bf16(x), b1 = RN_bf16(x - b0),
+//            b2 = RN_bf16(x - b0 - b1);
+//            a*b ~ sum of the six b_i*b_j with i + j <= 2 (kind::f16 with BF16, 6 MMAs)
+// The dropped terms are O(2^-22) (3xTF32) and O(2^-24) (BF16x3) relative to
+// |a*b|, so the result is FP32-accurate; these variants join the FP32 SIMT
+// family as further versions of the same operation.
+//
+// Pipeline (one CTA per 128 x BN output tile, 4 warps):
+//   a split kernel writes the planes K-major into the library workspace,
+//   warp 0 lane 0: TMA producer (3-D tensor maps over [plane][row][k], 128-byte
+//                  swizzle), full/empty mbarriers per stage;
+//   warp 1 lane 0: MMA issuer (tcgen05.mma, cta_group::1, M = 128, N = BN,
+//                  A and B K-major from shared memory descriptors), commits
+//                  to the stage's empty barrier and finally to acc_full;
+//   all 4 warps:   epilogue, tcgen05.ld of their 32 TMEM lanes (= rows),
+//                  alpha/beta, stores to C.
+// Every mbarrier wait is bounded; tensor memory is always freed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ptx.cuh"
+#include "simt.cuh"
+
+namespace pt {
+
+constexpr int kTcTf32 = 0;
+constexpr int kTcBf16x3 = 1;
+
+template <int KIND_, int BN_, int STAGES_>
+struct Tc {
+    static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_;
+    static constexpr int ELEM = KIND == kTcTf32 ? 4 : 2;  // bytes per plane element
+    static constexpr int P = KIND == kTcTf32 ? 2 : 3;     // planes per operand
+    static constexpr int BK = 128 / ELEM;                 // one 128-byte swizzle row per tile row
+    static constexpr int KSTEP = 32 / ELEM;               // K of one MMA instruction (32 bytes)
+    static constexpr int NPROD = KIND == kTcTf32 ? 3 : 6;
+    static constexpr int A_PLANE_BYTES = BM * 128;
+    static constexpr int B_PLANE_BYTES = BN * 128;
+    static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES);
+    static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
+    static constexpr int SMEM_BYTES = BAR_OFFSET + 8 * (2 * STAGES + 2) + 1024;
+    static constexpr int TMEM_COLS = BN;
+    static constexpr int THREADS = 128;
+    // Instruction descriptor: D = F32 (bits 4-5 = 1), A/B format (bits 7-9,
+    // 10-12: TF32 = 2, BF16 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+    // bit 17, M >> 4 at bit 24.
+    static constexpr uint32_t FMT = KIND == kTcTf32 ? 2u : 1u;
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+};
+
+// Plane pair (A plane, B plane) of product q, smallest terms first.
+template <int KIND>
+__device__ __forceinline__ void tc_product(int q, int &pa, int &pb) {
+    if constexpr (KIND == kTcTf32) {
+        constexpr int a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+        pa = a[q];
+        pb = b[q];
+    } else {
+        constexpr int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+        pa = a[q];
+        pb = b[q];
+    }
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this
+// layout), stride byte offset 1024 B between 8-row groups (bits 32-45),
+// descriptor version 1 (bit 46), swizzle mode 2 = 128 B (bits 61-63).  The
+// tile base is 1024-byte aligned, so the base-offset field is 0.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// ---- splitting --------------------------------------------------------------------
+// Round to nearest even on the TF32 grid (10 explicit mantissa bits) by bit
+// manipulation; infinities and NaNs keep their class.
+__device__ __forceinline__ float tf32_rne(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) != 0x7f800000u) u += 0xfffu + ((u >> 13) & 1u);
+    else if (u & 0x007fffffu) u |= 0x00400000u;
+    return __uint_as_float(u & 0xffffe000u);
+}
+
+__device__ __forceinline__ uint16_t bf16_rne_bits(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);
+    else if (u & 0x007fffffu) u |= 0x00400000u;
+    return (uint16_t)(u >> 16);
+}
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// Writes the planes of element (r, k) (r < rows, k < K).
+template <int KIND>
+__device__ __forceinline__ void split_store(unsigned char *ws, int64_t plane_bytes, int64_t pitch, int r, int k,
+                                            float x) {
+    if constexpr (KIND == kTcTf32) {
+        float *p = reinterpret_cast<float *>(ws) + (int64_t)r * pitch + k;
+        const float hi = tf32_rne(x);
+        const float lo = tf32_rne(x - hi);
+        p[0] = hi;
+        reinterpret_cast<float *>(ws + plane_bytes)[(int64_t)r * pitch + k] = lo;
+    } else {
+        const uint16_t b0 = bf16_rne_bits(x);
+        const float r1 = x - bf16_to_f32(b0);
+        const uint16_t b1 = bf16_rne_bits(r1);
+        const float r2 = r1 - bf16_to_f32(b1);
+        const uint16_t b2 = bf16_rne_bits(r2);
+        const int64_t off = (int64_t)r * pitch + k;
+        reinterpret_cast<uint16_t *>(ws)[off] = b0;
+        reinterpret_cast<uint16_t *>(ws + plane_bytes)[off] = b1;
+        reinterpret_cast<uint16_t *>(ws + 2 * plane_bytes)[off] = b2;
+    }
+}
+
+// Split of a logical rows x K operand X(r, k) into K-major planes.
+// trans == 0: X(r, k) at src[r*ld + k];  trans == 1: X(r, k) at src[k*ld + r].
+// 32 x 32 tiles through shared memory so both the read and the write are
+// coalesced.  Block (32, 8).
+template <int KIND>
+__global__ void __launch_bounds__(256) tc_split_kernel(const float *__restrict__ src, int64_t ld, int trans,
+                                                       int rows, int K, unsigned char *ws, int64_t plane_bytes,
+                                                       int64_t pitch) {
+    __shared__ float tile[32][33];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (trans) {
+        // read along r (contiguous), tile[k][r]
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+            const int k = k0 + ty + j, r = r0 + tx;
+            tile[ty + j][tx] = (k < K && r < rows) ? src[(int64_t)k * ld + r] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+            const int r = r0 + ty + j, k = k0 + tx;
+            if (r < rows && k < K) split_store<KIND>(ws, plane_bytes, pitch, r, k, tile[tx][ty + j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+            const int r = r0 + ty + j, k = k0 + tx;
+            if (r < rows && k < K) split_store<KIND>(ws, plane_bytes, pitch, r, k, src[(int64_t)r * ld + k]);
+        }
+    }
+}
+
+struct TcArgs {
+    float *C;
+    int64_t ldc;
+    int M, N, K;
+    float alpha, beta;
+    int vec4;  // C and ldc allow 16-byte stores
+    int *err;
+};
+
+template <class V>
+__global__ void __launch_bounds__(128, 1)
+    tc_sgemm_kernel(const TcArgs args, const __grid_constant__ CUtensorMap mapA,
+                    const __grid_constant__ CUtensorMap mapB) {
+    constexpr int STAGES = V::STAGES, BK = V::BK, BN = V::BN, P = V::P;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_fail, s_issued, s_consumed;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    const uint32_t full0 = sbase + V::BAR_OFFSET;
+    const uint32_t empty0 = full0 + 8 * STAGES;
+    const uint32_t accb = empty0 + 8 * STAGES;
+    const uint32_t tslot = accb + 8;
+    const volatile uint32_t *tslot_ptr =
+        reinterpret_cast<const volatile uint32_t *>(smem_raw + (tslot - raw));
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * V::BM, n0 = blockIdx.x * BN;
+    const int nkt = (args.K + BK - 1) / BK;
+
+    if (tid == 0) {
+        prefetch_tensormap(&mapA);
+        prefetch_tensormap(&mapB);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        fence_mbarrier_init();
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(tslot, V::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot_ptr;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int kt = 0;
+        for (; kt < nkt; ++kt) {
+            const int s = kt % STAGES, u = kt / STAGES;
+            if (kt >= STAGES && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)((u - 1) & 1), kWaitLimitNs)) {
+                s_fail = 1;
+                break;
+            }
+            const uint32_t st = sbase + s * V::STAGE_BYTES;
+            mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::STAGE_BYTES);
+#pragma unroll
+            for (int p = 0; p < P; ++p) tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, kt * BK, m0, p);
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s, kt * BK, n0, p);
+        }
+        s_issued = kt;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        int kt = 0;
+        for (; kt < nkt; ++kt) {
+            const int s = kt % STAGES, u = kt / STAGES;
+            if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = sbase + s * V::STAGE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
+#pragma unroll
+                for (int q = 0; q < V::NPROD; ++q) {
+                    int pa, pb;
+                    tc_product<V::KIND>(q, pa, pb);
+                    const uint64_t ad = sw128_kmajor_desc(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                    const uint64_t bd =
+                        sw128_kmajor_desc(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) + (uint64_t)(2 * kk);
+                    tc_mma<V::KIND>(tmem, ad, bd, V::IDESC, (kt | kk | q) != 0 ? 1u : 0u);
+                }
+            }
+            tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
+        }
+        tc_commit(accb);  // accumulator complete (also after a failure: drains issued MMAs)
+        s_consumed = kt;
+    }
+    __syncthreads();
+
+    const bool ok = mbar_wait_bounded(accb, 0u, kWaitLimitNs);
+    const bool failed = __syncthreads_or(!ok || s_fail);
+    tc_fence_after();
+    if (!failed) {
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
+        const float alpha = args.alpha, beta = args.beta;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tb + (uint32_t)c0, r);
+            const int col = n0 + c0;
+            if (row < args.M && col < args.N) {
+                float *cp = args.C + (int64_t)row * args.ldc + col;
+                const int ncol = args.N - col;
+                if (ncol >= 32 && args.vec4) {
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4) {
+                        float4 v = make_float4(alpha * __uint_as_float(r[q]), alpha * __uint_as_float(r[q + 1]),
+                                               alpha * __uint_as_float(r[q + 2]), alpha * __uint_as_float(r[q + 3]));
+                        if (beta != 0.f) {
+                            const float4 o = *reinterpret_cast<const float4 *>(cp + q);
+                            v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+                        }
+                        *reinterpret_cast<float4 *>(cp + q) = v;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        if (q < ncol) {
+                            const float v = alpha * __uint_as_float(r[q]);
+                            cp[q] = (beta != 0.f) ? v + beta * cp[q] : v;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (failed && tid == 0) {
+        if (args.err) atomicOr(args.err, 1);
+        // TMA copies issued but never consumed must land before the CTA exits.
+        for (int q = s_consumed; q < s_issued; ++q)
+            (void)mbar_wait_bounded(full0 + 8 * (q % STAGES), (uint32_t)((q / STAGES) & 1), kWaitLimitNs);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, V::TMEM_COLS);
+    }
+}
+
+}  // namespace pt

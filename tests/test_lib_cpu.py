@@ -36,13 +36,23 @@ def test_library_exports_every_declared_symbol():
 
 def test_registry_rules():
     n = pt.num_variants()
-    assert 300 <= n <= 400
+    assert 300 <= n <= 420
     names = set()
+    simt = []
     for i in range(n):
         d = pt.variant(i)
         assert d["id"] == i
         assert d["name"] not in names
         names.add(d["name"])
+        assert pt.variant_by_name(d["name"]) == i
+        assert d["smem_bytes"] <= 232448
+        if d["kind"] != 0:
+            # split-precision tensor-core variants: 128-row tiles, TMA, any layout
+            assert d["kind"] in (1, 2) and d["bm"] == 128 and d["bn"] in (64, 128, 256)
+            assert d["loader"] == 1 and d["trans_mask"] == 15 and d["threads"] == 128
+            assert d["bk"] * (4 if d["kind"] == 1 else 2) == 128  # one 128-byte swizzle row
+            continue
+        simt.append(i)
         assert d["bm"] % d["wm"] == 0 and d["bn"] % d["wn"] == 0
         assert (d["wm"] // d["tm"]) * (d["wn"] // d["tn"]) * d["kl"] == 32
         assert d["threads"] == 32 * (d["bm"] // d["wm"]) * (d["bn"] // d["wn"])
@@ -51,12 +61,13 @@ def test_registry_rules():
         assert d["smem_bytes"] <= 232448
         assert d["bm"] % d["splitk"] == 0
         assert d["tm"] * d["tn"] <= 64
-        assert pt.variant_by_name(d["name"]) == i
+    assert {pt.variant(i)["kind"] for i in range(n)} == {0, 1, 2}
+    assert all(pt.variant(i)["kind"] == 0 for i in range(len(simt)))  # SIMT family first
     d0 = pt.variant(pt.default_variant())
     assert (d0["bm"], d0["bn"], d0["bk"], d0["vec"], d0["loader"], d0["trans_mask"]) == (128, 128, 8, 1, 0, 15)
     for key, values in (("splitk", {1, 2, 4, 8}), ("loader", {0, 1}), ("vec", {1, 2, 4}),
                         ("stages", {2, 3, 4}), ("bk", {8, 16, 32}), ("kl", {1, 2, 4}), ("fma2", {0, 1})):
-        assert {pt.variant(i)[key] for i in range(n)} == values, key
+        assert {pt.variant(i)[key] for i in simt} == values, key
 
 
 def test_argument_validation_without_gpu():
