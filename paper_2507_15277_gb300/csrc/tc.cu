@@ -152,8 +152,8 @@ VariantEntry tc_entry(const char *name) {
 // Tensor-core variants appended to the registry after the SIMT family.
 std::vector<VariantEntry> tc_variants() {
     return {
-        tc_entry<Tc<kTcTf32, 256, 2>>("tc3xtf32_m128n256_p2"),
         tc_entry<Tc<kTcTf32, 128, 3>>("tc3xtf32_m128n128_p3"),
+        tc_entry<Tc<kTcTf32, 128, 2>>("tc3xtf32_m128n128_p2"),
         tc_entry<Tc<kTcTf32, 64, 4>>("tc3xtf32_m128n64_p4"),
         tc_entry<Tc<kTcBf16x3, 128, 2>>("tcbf16x3_m128n128_p2"),
         tc_entry<Tc<kTcBf16x3, 64, 3>>("tcbf16x3_m128n64_p3"),

@@ -12,15 +12,20 @@
 // |a*b|, so the result is FP32-accurate; these variants join the FP32 SIMT
 // family as further versions of the same operation.
 //
-// Pipeline (one CTA per 128 x BN output tile, 4 warps):
-//   a split kernel writes the planes K-major into the library workspace,
-//   warp 0 lane 0: TMA producer (3-D tensor maps over [plane][row][k], 128-byte
-//                  swizzle), full/empty mbarriers per stage;
-//   warp 1 lane 0: MMA issuer (tcgen05.mma, cta_group::1, M = 128, N = BN,
-//                  A and B K-major from shared memory descriptors), commits
-//                  to the stage's empty barrier and finally to acc_full;
-//   all 4 warps:   epilogue, tcgen05.ld of their 32 TMEM lanes (= rows),
-//                  alpha/beta, stores to C.
+// Pipeline (one CTA per 128 x BN output tile):
+//   a split kernel writes the planes K-major into the library workspace;
+//   producer warp (one lane): TMA loads of every plane's tile (3-D tensor maps
+//                  over [plane][row][k], 128-byte swizzle), full/empty
+//                  mbarriers per stage;
+//   MMA warp (one lane): tcgen05.mma (cta_group::1, M = 128, N = BN, A and B
+//                  K-major from shared-memory descriptors) into one of two
+//                  TMEM accumulators; every 128 values of k (a "chunk") the
+//                  accumulator is committed and the other buffer is used;
+//   epilogue warps (4 per 128 columns): tcgen05.ld of their 32 TMEM lanes
+//                  (= rows) after each chunk, added into FP32 registers with
+//                  IEEE round-to-nearest ("promotion": the tensor core's own
+//                  accumulation, which is not IEEE round-to-nearest, then
+//                  spans only 128 products), alpha/beta, stores to C.
 // Every mbarrier wait is bounded; tensor memory is always freed.
 #pragma once
 
@@ -43,13 +48,23 @@ struct Tc {
     static constexpr int BK = 128 / ELEM;                 // one 128-byte swizzle row per tile row
     static constexpr int KSTEP = 32 / ELEM;               // K of one MMA instruction (32 bytes)
     static constexpr int NPROD = KIND == kTcTf32 ? 3 : 6;
+    // Promotion: the tensor-core accumulator is restarted every CHUNK_KT
+    // k-tiles (128 values of k) and added into FP32 registers with IEEE
+    // round-to-nearest, so the accumulation error grows with 128, not K.
+    static constexpr int CHUNK_KT = 128 / BK;
     static constexpr int A_PLANE_BYTES = BM * 128;
     static constexpr int B_PLANE_BYTES = BN * 128;
     static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES);
     static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
-    static constexpr int SMEM_BYTES = BAR_OFFSET + 8 * (2 * STAGES + 2) + 1024;
-    static constexpr int TMEM_COLS = BN;
-    static constexpr int THREADS = 128;
+    static constexpr int SMEM_BYTES = BAR_OFFSET + 8 * (2 * STAGES + 5) + 1024;
+    static constexpr int TMEM_COLS = 2 * BN;  // two accumulator buffers
+    // Epilogue warps: 4 per 128 columns (a warp reads its 32 TMEM lanes), each
+    // thread owns one row and COLS columns; then one producer and one MMA warp.
+    static constexpr int COL_GROUPS = BN >= 128 ? BN / 128 : 1;
+    static constexpr int COLS = BN / COL_GROUPS;
+    static constexpr int EPI_WARPS = 4 * COL_GROUPS;
+    static constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
+    static constexpr int THREADS = 32 * (EPI_WARPS + 2);
     // Instruction descriptor: D = F32 (bits 4-5 = 1), A/B format (bits 7-9,
     // 10-12: TF32 = 2, BF16 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
     // bit 17, M >> 4 at bit 24.
@@ -57,6 +72,7 @@ struct Tc {
     static constexpr uint32_t IDESC =
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
+    static_assert(TMEM_COLS <= 512, "tensor memory columns");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
@@ -169,24 +185,27 @@ struct TcArgs {
 };
 
 template <class V>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(V::THREADS, 1)
     tc_sgemm_kernel(const TcArgs args, const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapB) {
-    constexpr int STAGES = V::STAGES, BK = V::BK, BN = V::BN, P = V::P;
+    constexpr int STAGES = V::STAGES, BK = V::BK, BN = V::BN, P = V::P, CKT = V::CHUNK_KT, COLS = V::COLS;
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_fail, s_issued, s_consumed;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
-    const uint32_t full0 = sbase + V::BAR_OFFSET;
-    const uint32_t empty0 = full0 + 8 * STAGES;
-    const uint32_t accb = empty0 + 8 * STAGES;
-    const uint32_t tslot = accb + 8;
+    const uint32_t full0 = sbase + V::BAR_OFFSET;  // STAGES: TMA landed
+    const uint32_t empty0 = full0 + 8 * STAGES;    // STAGES: MMAs done reading
+    const uint32_t accf0 = empty0 + 8 * STAGES;    // 2: accumulator buffer ready
+    const uint32_t acce0 = accf0 + 16;             // 2: accumulator buffer drained
+    const uint32_t doneb = acce0 + 16;             // every issued MMA finished
+    const uint32_t tslot = doneb + 8;
     const volatile uint32_t *tslot_ptr =
         reinterpret_cast<const volatile uint32_t *>(smem_raw + (tslot - raw));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * V::BM, n0 = blockIdx.x * BN;
     const int nkt = (args.K + BK - 1) / BK;
+    const int nchunks = (nkt + CKT - 1) / CKT;
 
     if (tid == 0) {
         prefetch_tensormap(&mapA);
@@ -195,7 +214,11 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, V::EPI_WARPS);
+        }
+        mbar_init(doneb, 1);
         fence_mbarrier_init();
         s_fail = 0;
         s_issued = 0;
@@ -210,100 +233,139 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot_ptr;
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        int kt = 0;
-        for (; kt < nkt; ++kt) {
-            const int s = kt % STAGES, u = kt / STAGES;
-            if (kt >= STAGES && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)((u - 1) & 1), kWaitLimitNs)) {
-                s_fail = 1;
-                break;
+    float racc[COLS];
+#pragma unroll
+    for (int j = 0; j < COLS; ++j) racc[j] = 0.f;
+    bool epi_ok = true;
+
+    if (warp == V::PRODUCER_WARP) {
+        if (lane == 0) {
+            int kt = 0;
+            for (; kt < nkt; ++kt) {
+                const int s = kt % STAGES, u = kt / STAGES;
+                if (kt >= STAGES && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)((u - 1) & 1), kWaitLimitNs)) {
+                    s_fail = 1;
+                    break;
+                }
+                const uint32_t st = sbase + s * V::STAGE_BYTES;
+                mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::STAGE_BYTES);
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, kt * BK, m0, p);
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s, kt * BK, n0,
+                                p);
             }
-            const uint32_t st = sbase + s * V::STAGE_BYTES;
-            mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::STAGE_BYTES);
-#pragma unroll
-            for (int p = 0; p < P; ++p) tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, kt * BK, m0, p);
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-                tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s, kt * BK, n0, p);
+            s_issued = kt;
         }
-        s_issued = kt;
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        int kt = 0;
-        for (; kt < nkt; ++kt) {
-            const int s = kt % STAGES, u = kt / STAGES;
-            if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs)) {
-                s_fail = 1;
+    } else if (warp == V::MMA_WARP) {
+        if (lane == 0) {
+            int kt = 0;
+            for (; kt < nkt; ++kt) {
+                const int s = kt % STAGES, u = kt / STAGES;
+                const int c = kt / CKT, b = c & 1;
+                const bool first = (kt % CKT) == 0;
+                // Buffer b was last used by chunk c - 2; wait until it is drained.
+                if (first && c >= 2 &&
+                    !mbar_wait_bounded(acce0 + 8 * b, (uint32_t)(((c >> 1) - 1) & 1), kWaitLimitNs)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = sbase + s * V::STAGE_BYTES;
+                const uint32_t dt = tmem + (uint32_t)(b * BN);
+#pragma unroll
+                for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
+#pragma unroll
+                    for (int q = 0; q < V::NPROD; ++q) {
+                        int pa, pb;
+                        tc_product<V::KIND>(q, pa, pb);
+                        const uint64_t ad = sw128_kmajor_desc(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                        const uint64_t bd =
+                            sw128_kmajor_desc(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) + (uint64_t)(2 * kk);
+                        tc_mma<V::KIND>(dt, ad, bd, V::IDESC, (first && kk == 0 && q == 0) ? 0u : 1u);
+                    }
+                }
+                tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
+                if ((kt % CKT) == CKT - 1 || kt == nkt - 1) tc_commit(accf0 + 8 * b);  // chunk c complete
+            }
+            tc_commit(doneb);  // every MMA issued so far (also after a failure)
+            s_consumed = kt;
+        }
+    } else {
+        // Epilogue warps: drain each chunk's accumulator into FP32 registers.
+        const int sub = warp & 3, grp = warp >> 2;
+        const uint32_t lane_base = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(grp * COLS);
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            const bool ok = mbar_wait_bounded(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), kWaitLimitNs);
+            if (!__all_sync(0xffffffffu, ok)) {
+                epi_ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t st = sbase + s * V::STAGE_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
+            for (int j = 0; j < COLS; j += 32) {
+                uint32_t r[32];
+                tmem_ld32(lane_base + (uint32_t)(b * BN + j), r);
 #pragma unroll
-                for (int q = 0; q < V::NPROD; ++q) {
-                    int pa, pb;
-                    tc_product<V::KIND>(q, pa, pb);
-                    const uint64_t ad = sw128_kmajor_desc(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
-                    const uint64_t bd =
-                        sw128_kmajor_desc(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) + (uint64_t)(2 * kk);
-                    tc_mma<V::KIND>(tmem, ad, bd, V::IDESC, (kt | kk | q) != 0 ? 1u : 0u);
-                }
+                for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
             }
-            tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * b);
         }
-        tc_commit(accb);  // accumulator complete (also after a failure: drains issued MMAs)
-        s_consumed = kt;
     }
     __syncthreads();
+    if (!epi_ok) s_fail = 1;
+    __syncthreads();
+    const bool failed = s_fail != 0;
 
-    const bool ok = mbar_wait_bounded(accb, 0u, kWaitLimitNs);
-    const bool failed = __syncthreads_or(!ok || s_fail);
-    tc_fence_after();
-    if (!failed) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
+    if (!failed && warp < V::EPI_WARPS) {
+        const int row = m0 + (warp & 3) * 32 + lane;
+        const int cbase = n0 + (warp >> 2) * COLS;
         const float alpha = args.alpha, beta = args.beta;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            uint32_t r[32];
-            tmem_ld32(tb + (uint32_t)c0, r);
-            const int col = n0 + c0;
-            if (row < args.M && col < args.N) {
-                float *cp = args.C + (int64_t)row * args.ldc + col;
-                const int ncol = args.N - col;
-                if (ncol >= 32 && args.vec4) {
+        if (row < args.M && cbase < args.N) {
+            float *cp = args.C + (int64_t)row * args.ldc + cbase;
+            const int ncol = args.N - cbase;
+            if (ncol >= COLS && args.vec4) {
 #pragma unroll
-                    for (int q = 0; q < 32; q += 4) {
-                        float4 v = make_float4(alpha * __uint_as_float(r[q]), alpha * __uint_as_float(r[q + 1]),
-                                               alpha * __uint_as_float(r[q + 2]), alpha * __uint_as_float(r[q + 3]));
-                        if (beta != 0.f) {
-                            const float4 o = *reinterpret_cast<const float4 *>(cp + q);
-                            v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
-                        }
-                        *reinterpret_cast<float4 *>(cp + q) = v;
+                for (int q = 0; q < COLS; q += 4) {
+                    float4 v = make_float4(alpha * racc[q], alpha * racc[q + 1], alpha * racc[q + 2],
+                                           alpha * racc[q + 3]);
+                    if (beta != 0.f) {
+                        const float4 o = *reinterpret_cast<const float4 *>(cp + q);
+                        v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
                     }
-                } else {
+                    *reinterpret_cast<float4 *>(cp + q) = v;
+                }
+            } else {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        if (q < ncol) {
-                            const float v = alpha * __uint_as_float(r[q]);
-                            cp[q] = (beta != 0.f) ? v + beta * cp[q] : v;
-                        }
+                for (int q = 0; q < COLS; ++q) {
+                    if (q < ncol) {
+                        const float v = alpha * racc[q];
+                        cp[q] = (beta != 0.f) ? v + beta * cp[q] : v;
                     }
                 }
             }
+        }
+    }
+    if (tid == 0) {
+        // No MMA may still write tensor memory when it is freed, and no TMA
+        // copy may still be landing when the CTA exits.
+        if (!mbar_wait_bounded(doneb, 0u, kWaitLimitNs)) s_fail = 1;
+        if (s_fail) {
+            if (args.err) atomicOr(args.err, 1);
+            for (int q = s_consumed; q < s_issued; ++q)
+                (void)mbar_wait_bounded(full0 + 8 * (q % STAGES), (uint32_t)((q / STAGES) & 1), kWaitLimitNs);
         }
     }
     tc_fence_before();
-    __syncthreads();
-    if (failed && tid == 0) {
-        if (args.err) atomicOr(args.err, 1);
-        // TMA copies issued but never consumed must land before the CTA exits.
-        for (int q = s_consumed; q < s_issued; ++q)
-            (void)mbar_wait_bounded(full0 + 8 * (q % STAGES), (uint32_t)((q / STAGES) & 1), kWaitLimitNs);
-    }
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();

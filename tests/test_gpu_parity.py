@@ -180,7 +180,7 @@ def test_config_256_fixed_variant():
     assert err <= TOL_FP32, err
 
 
-@pytest.mark.parametrize("name_part", ["sk1_cpm", "sk4_cpk", "tmk", "kl2", "sk8"])
+@pytest.mark.parametrize("name_part", ["sk1_cpm", "sk4_cpk", "tmk", "kl2", "sk8", "tc3xtf32", "tcbf16x3"])
 def test_full_size_sampled_rows(name_part):
     """4096^3 (largest sweep shape) on sampled rows, inputs U[-1,1]."""
     M = N = K = 4096
