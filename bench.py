@@ -141,6 +141,39 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def measured_peaks():
+    """Measured peaks of this GPU pool (MEASURED_PEAKS.json), if present."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_for(kernel, shape):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and
+    shape (profiles/traffic.json), or None when no capture of the current
+    kernel source exists."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2507_15277_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("simt.cuh", "tc.cuh", "ptx.cuh"):
+        with open(os.path.join(src, name), "rb") as f:
+            h.update(f.read())
+    for e in rec.get("captures", []):
+        if e.get("kernel") == kernel and tuple(e.get("shape", ())) == tuple(shape) and \
+                e.get("source_sha256") == h.hexdigest():
+            return e.get("dram_bytes")
+    return None
+
+
 # ---- CPU oracle baseline -----------------------------------------------------------------
 def cpu_oracle_sample(shapes, rows_per_shape, seed_base=1000):
     """Times the FP64 CPU oracle on the first `rows_per_shape` rows of every
@@ -388,17 +421,35 @@ def main():
     dom = max(range(len(shapes)), key=lambda i: shape_ms[i])
     M, N, K = shapes[dom]
     dom_ms = shape_ms[dom]
-    achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
     f_max = 2070.0
-    peak = sms * 128 * 2 * f_max * 1e6 / 1e12
+    fp32_peak = sms * 128 * 2 * f_max * 1e6 / 1e12
     f_med = clk.get("sm_mhz")
-    roofline = {
-        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-        "traffic": None, "kernel": pt.variant(picks[dom])["name"], "shape": [M, N, K],
-        "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, f_max),
-        "frac_at_sampled_clock": (achieved / (sms * 256 * f_med * 1e6 / 1e12)) if f_med else None,
-        "share_of_step": dom_ms / sum(shape_ms),
-    }
+    peaks = measured_peaks()
+    dvar = pt.variant(picks[dom])
+    if dvar["kind"] == 0:
+        # FP32 FMA on the CUDA cores: 2MNK flops against the FP32 ALU peak.
+        achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, f_max),
+                    "frac_at_sampled_clock": (achieved / (sms * 256 * f_med * 1e6 / 1e12)) if f_med else None}
+    else:
+        # Split-precision tensor-core kernel: the tensor pipe executes
+        # (products per FP32 product) x 2MNK flops of TF32 or BF16 MMAs.
+        nprod, ratio, dt = (3, 1.1 / 2.25, "tf32") if dvar["kind"] == 1 else (6, 1.0, "bf16")
+        achieved = nprod * flops[dom] / (dom_ms * 1e-3) / 1e12
+        bf16 = peaks.get("bf16_tflops") or 1900.0
+        bf16_sus = peaks.get("bf16_tflops_sustained") or 1700.0
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": bf16 * ratio, "unit": "TFLOP/s",
+                    "peak_basis": "%s dense tensor peak = measured cuBLAS bf16 burst %.1f TFLOP/s (of measured) x "
+                                  "nominal %s/bf16 ratio %.3f; achieved counts %d MMA products per FP32 product"
+                                  % (dt, bf16, dt, ratio, nprod),
+                    "frac_vs_sustained": achieved / (bf16_sus * ratio),
+                    "fp32_equivalent_tflops": flops[dom] / (dom_ms * 1e-3) / 1e12,
+                    "fp32_equivalent_frac_of_fp32_peak": flops[dom] / (dom_ms * 1e-3) / 1e12 / fp32_peak}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    roofline.update({"traffic": traffic_for(dvar["name"], (M, N, K)), "kernel": dvar["name"], "shape": [M, N, K],
+                     "share_of_step": dom_ms / sum(shape_ms)})
+    peak = fp32_peak
 
     # cuBLAS SGEMM (FP32, TF32 off) on the same shapes, as context.
     torch.backends.cuda.matmul.allow_tf32 = False
