@@ -194,6 +194,32 @@ int pt_selected_variant(char transA, char transB, int64_t M, int64_t N, int64_t 
  * manifest.  Synchronises the devices that hold a workspace. */
 int pt_shutdown(void);
 
+/* Allocation-free SGEMM (the paper has no counterpart; this is a library
+ * convenience).  For callers that cannot allocate device memory during their
+ * GEMM calls: programs whose device memory is handed to their own pool
+ * allocator at start-up and which forbid raw cudaMalloc, latency-critical
+ * loops in which an allocation (that may synchronise the device) is not
+ * acceptable, and hosts that only run with memory reserved in advance.
+ * Same operation and arguments as pt_sgemm; it always runs the 3xTF32
+ * tensor-core kernel (128 x 128 tiles), with the split planes in a fixed
+ * array of PT_NOALLOC_SCRATCH_BYTES bytes of device memory that belongs to
+ * the library image (every GPU that loads the library holds it until the
+ * process exits).  It calls no cudaMalloc, cudaFree or allocating routine.
+ * Limit: 2 * (M + N) * round_up(K, 4) * 4 bytes (plus up to 1 KiB of
+ * alignment) must not exceed PT_NOALLOC_SCRATCH_BYTES, else PT_EINVAL and
+ * nothing is launched.  The first call on a device looks up the array's
+ * device address on that device (the device must be current) and sets the
+ * kernel's shared-memory attribute; make that first call before any other
+ * use on the device that must not do such set-up.  Every call shares the one
+ * array: calls whose kernels overlap on the GPU (e.g. on two streams without
+ * ordering between them) race on it and give wrong results.  A bounded
+ * device wait that gives up leaves C unwritten (not reported through
+ * pt_device_status). */
+#define PT_NOALLOC_SCRATCH_BYTES (64u << 20)
+int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K,
+                            float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                            float beta, float *C, int64_t ldc, void *stream);
+
 /* Device-side error word set by kernels whose bounded waits gave up
  * (PT_ETIMEOUT) on the current device; reading clears it.  Synchronises the
  * device. */

@@ -86,6 +86,7 @@ SIGNATURES = {
                                            _p, _i64]),
     "pt_device_status": (ctypes.c_int, []),
     "pt_shutdown": (ctypes.c_int, []),
+    "pt_sgemm_3xtf32_noalloc": (ctypes.c_int, _GEMM_ARGS),
 }
 
 _lib = None

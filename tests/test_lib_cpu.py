@@ -49,7 +49,8 @@ def test_registry_rules():
         if d["kind"] != 0:
             # split-precision tensor-core variants: 128-row tiles, TMA, any layout
             assert d["kind"] in (1, 2) and d["bm"] == 128 and d["bn"] in (64, 128, 256)
-            assert d["loader"] == 1 and d["trans_mask"] == 15 and d["threads"] == 128
+            assert d["loader"] == 1 and d["trans_mask"] == 15
+            assert d["threads"] == 32 * (4 * max(1, d["bn"] // 128) + 2)  # epilogue + producer + MMA warps
             assert d["bk"] * (4 if d["kind"] == 1 else 2) == 128  # one 128-byte swizzle row
             continue
         simt.append(i)
