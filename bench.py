@@ -55,7 +55,79 @@ def parse():
     p.add_argument("--single", default=None, metavar="M,N,K",
                    help="profiling mode: run one variant (--variant) on one shape, no tuning")
     p.add_argument("--variant", default=None, help="variant name for --single")
+    p.add_argument("--report", default=None, choices=["splitprec"],
+                   help="splitprec: tensor-core split-precision vs FP32 SIMT on the split-precision shapes")
     return p.parse_args()
+
+
+def report_splitprec(args):
+    """Split-precision tensor-core variants vs the FP32 SIMT family on
+    M=N=K in {1024, 4096, 8192}, 8192x8192x256 and 256x8192x8192, inputs of
+    random sign with magnitudes 2^U[-10,10] (seed 3): TFLOP/s of the fastest
+    variant of each kind (timed by the tuner) and its normalised error
+    against the FP64 oracle on 64 sampled rows; TF32 cuBLAS throughput at
+    8192^3 as the measured TF32 reference."""
+    import numpy as np
+    import torch
+
+    import paper_2507_15277_gb300 as pt
+    from oracle import gemm as og
+    from oracle.checks import normalised_error
+    from workloads import matrix, split_precision_shapes
+    dev = torch.device("cuda", 0)
+    shapes = split_precision_shapes()
+    vs = pt.variants()
+    ids = [v["id"] for v in vs if v["kind"] != 0 or (v["fma2"] and v["bm"] * v["bn"] >= 4096 and v["splitk"] <= 4)]
+    out_dir = args.out_dir or tempfile.mkdtemp(prefix="ptsplit_")
+    os.makedirs(out_dir, exist_ok=True)
+    table = os.path.join(out_dir, "splitprec_table.csv")
+    t0 = time.perf_counter()
+    pt.tune(shapes, table, ids=ids, reps_min=3, reps_max=10, target_ms=10.0)
+    tune_s = time.perf_counter() - t0
+    import csv
+    rows = list(csv.DictReader(open(table)))
+    res = []
+    for si, (M, N, K) in enumerate(shapes):
+        best = {}
+        for r in rows:
+            if (int(r["M"]), int(r["N"]), int(r["K"])) != (M, N, K) or not int(r["valid"]):
+                continue
+            kind = pt.variant(pt.variant_by_name(r["variant"]))["kind"]
+            t = float(r["median_ms"])
+            if kind not in best or t < best[kind][0]:
+                best[kind] = (t, r["variant"])
+        A = matrix("logu", 3, M, K)
+        B = matrix("logu", 4, K, N)
+        sample = np.sort(np.random.default_rng(si).choice(M, min(64, M), replace=False))
+        ref = og.gemm(A, B, rows=sample)
+        Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        entry = {"shape": [M, N, K]}
+        for kind, label in ((0, "fp32_simt"), (1, "3xtf32"), (2, "bf16x3")):
+            if kind not in best:
+                continue
+            t, name = best[kind]
+            C = pt.sgemm(Ad, Bd, variant=pt.variant_by_name(name))
+            torch.cuda.synchronize()
+            err = normalised_error(C[sample].cpu().numpy(), ref, K, np.abs(A).max(), np.abs(B).max())
+            entry[label] = {"variant": name, "ms": t, "tflops": 2.0 * M * N * K / (t * 1e-3) / 1e12, "err": err}
+        del Ad, Bd
+        res.append(entry)
+    torch.backends.cuda.matmul.allow_tf32 = True
+    X = torch.randn(8192, 8192, device=dev)
+    Y = torch.randn(8192, 8192, device=dev)
+    for _ in range(3):
+        torch.matmul(X, Y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        torch.matmul(X, Y)
+    e1.record()
+    torch.cuda.synchronize()
+    tf32 = 10 * 2.0 * 8192 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    torch.backends.cuda.matmul.allow_tf32 = False
+    print(json.dumps({"mode": "splitprec", "inputs": "sign * 2^U[-10,10], seed 3; error on 64 sampled rows",
+                      "tune_s": tune_s, "tf32_cublas_tflops_8192": tf32, "shapes": res}))
+    return 0
 
 
 def single(args):
@@ -233,6 +305,8 @@ def main():
         return reference_arm(args)
     if args.single:
         return single(args)
+    if args.report == "splitprec":
+        return report_splitprec(args)
 
     import numpy as np
     import torch
