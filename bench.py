@@ -365,6 +365,24 @@ def main():
             rs[k] = (statistics.mean(vals), statistics.pstdev(vals))
         info["random_splits"] = rs
         info["selection"] = sel
+        # The paper's alternative implementations (Section IV-C) on the same
+        # split: held-out best-of-set and selector-realised scores and the
+        # time each selection takes.
+        comp = {}
+        for mname, method in (("portabilitytune", pt.PT_SELECT_AUTO), ("kmeans", pt.PT_SELECT_KMEANS),
+                              ("tree", pt.PT_SELECT_TREE)):
+            comp[mname] = {}
+            for k in (1, 2, 4, 8):
+                man = os.path.join(out_dir, "sel_%s_k%d.json" % (mname, k))
+                t0 = time.perf_counter()
+                ids, g_train = pt.select(table, train, k, method=method, manifest=man)
+                dt = time.perf_counter() - t0
+                comp[mname]["k%d" % k] = {
+                    "n_ids": len(ids), "train_pct": 100 * g_train,
+                    "heldout_pct": 100 * pt.score(table, held, ids),
+                    "heldout_selector_pct": 100 * pt.score(table, held, mode=pt.PT_SCORE_SELECTOR, manifest=man),
+                    "select_s": dt}
+        info["selectors"] = comp
     barrier()
     manifest = os.path.join(out_dir, "kappa_k%d.json" % args.k)
     pt.load_manifest(manifest)
@@ -574,6 +592,7 @@ def main():
         "random_splits_heldout_pct": {("k%d" % k): [100 * m, 100 * sd] for k, (m, sd) in
                                       info.get("random_splits", {}).items()},
         "kappa": sel.get(args.k, {}).get("names"),
+        "selectors": info.get("selectors"),
         "tuning": {"tune_s": info.get("tune_s"), "select_s": info.get("select_s"), "table": table},
         "per_shape": [{"shape": list(s), "ms": round(ms, 5), "tflops": round(f / (ms * 1e-3) / 1e12, 3),
                        "variant": pt.variant(p)["name"], "cublas_tflops": round(f / (cm * 1e-3) / 1e12, 3)}

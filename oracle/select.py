@@ -150,3 +150,179 @@ def nearest_shape(query, shapes) -> int:
         if best_d is None or d < best_d:
             best, best_d = i, d
     return best
+
+
+# ---- alternative selections (Section IV-C) ---------------------------------------------
+#
+# Both work on the training shapes' performance vectors: shape s is the point
+# perf[:, s] with perf[v, s] = t_best(s) / t(v, s) (0 where v is invalid), a
+# point in |K|-dimensional space (one coordinate per variant).
+#
+# Random draws come from SplitMix64 (the same published definition as the
+# input generator): draw i of seed `seed` is mix(seed + (i + 1) * gamma);
+# u = (x >> 11) * 2^-53 is uniform on [0, 1).
+
+def _splitmix_u(seed: int, i: int) -> float:
+    m = (1 << 64) - 1
+    z = (seed + (i + 1) * 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    z = z ^ (z >> 31)
+    return (z >> 11) * 2.0 ** -53
+
+
+def performance_vectors(times: np.ndarray, shapes) -> list:
+    """points[j][v] = t_best(s_j) / t(v, s_j), 0 for an invalid entry (plain lists)."""
+    t = np.asarray(times, dtype=np.float64)
+    tb = per_shape_best(t)
+    pts = []
+    for s in shapes:
+        pts.append([float(tb[s] / t[v, s]) if math.isfinite(t[v, s]) else 0.0 for v in range(t.shape[0])])
+    return pts
+
+
+def _sqdist(a, b) -> float:
+    d = 0.0
+    for x, y in zip(a, b):
+        d += (x - y) * (x - y)
+    return d
+
+
+def _argmax_first(vec) -> int:
+    best = 0
+    for v in range(1, len(vec)):
+        if vec[v] > vec[best]:
+            best = v
+    return best
+
+
+def kmeans_select(times: np.ndarray, k: int, shapes, seed: int = 0, max_iter: int = 100):
+    """k-means selection (Section IV-C-2).
+
+    Points: the training shapes' performance vectors.  Initial centroids by
+    k-means++ (first point: floor(u_0 * n); each next point with probability
+    proportional to its squared distance to the nearest chosen centroid,
+    using draw 1, 2, ...; if every distance is 0, the lowest unchosen index).
+    Lloyd iterations: each point to its nearest centroid (ties to the lower
+    centroid), centroids = cluster means (an empty cluster keeps its
+    centroid), until no assignment changes or max_iter.  Each centroid then
+    contributes its highest-performing variant (ties to the lower id).
+    Returns (sorted distinct variant ids, final assignment of the points).
+    """
+    pts = performance_vectors(times, shapes)
+    n = len(pts)
+    k = min(k, n)
+    draws = 0
+    first = int(_splitmix_u(seed, draws) * n) if n else 0
+    draws += 1
+    centers = [list(pts[first])]
+    chosen = [first]
+    while len(centers) < k:
+        d2 = [min(_sqdist(p, c) for c in centers) for p in pts]
+        total = 0.0
+        for x in d2:
+            total += x
+        if total <= 0.0:
+            nxt = next(i for i in range(n) if i not in chosen)
+        else:
+            u = _splitmix_u(seed, draws) * total
+            acc, nxt = 0.0, n - 1
+            for i, x in enumerate(d2):
+                acc += x
+                if acc > u:
+                    nxt = i
+                    break
+        draws += 1
+        chosen.append(nxt)
+        centers.append(list(pts[nxt]))
+    assign = [-1] * n
+    for _ in range(max_iter):
+        changed = False
+        for i, p in enumerate(pts):
+            best, bd = 0, _sqdist(p, centers[0])
+            for c in range(1, len(centers)):
+                d = _sqdist(p, centers[c])
+                if d < bd:
+                    best, bd = c, d
+            if assign[i] != best:
+                assign[i] = best
+                changed = True
+        if not changed:
+            break
+        for c in range(len(centers)):
+            members = [pts[i] for i in range(n) if assign[i] == c]
+            if members:
+                dim = len(members[0])
+                mean = [0.0] * dim
+                for m in members:
+                    for v in range(dim):
+                        mean[v] += m[v]
+                centers[c] = [x / len(members) for x in mean]
+    ids = sorted({_argmax_first(c) for c in centers})
+    return ids, assign
+
+
+def tree_select(times: np.ndarray, k: int, shapes, features):
+    """Regression-tree selection (Section IV-C-3).
+
+    A regression tree maps an environment's features (here the log2 of its
+    M, N, K) to its performance vector, with squared error summed over the
+    vector's coordinates.  It is grown best-first: the leaf whose best split
+    removes the most squared error is split next, until it has k leaves or no
+    split removes any error.  Candidate splits: every feature, thresholds
+    halfway between consecutive distinct values; ties go to the lower feature
+    index, then the lower threshold, then the earlier leaf.  Each leaf
+    contributes the highest-performing variant of its mean vector (ties to
+    the lower id).  Returns (sorted distinct ids, leaves) with leaves a list
+    of (member point indices, variant).
+    """
+    pts = performance_vectors(times, shapes)
+    feats = [list(features[s]) for s in shapes]
+    dim = len(pts[0]) if pts else 0
+
+    def sse(idx):
+        if not idx:
+            return 0.0
+        mean = [0.0] * dim
+        for i in idx:
+            for v in range(dim):
+                mean[v] += pts[i][v]
+        mean = [x / len(idx) for x in mean]
+        e = 0.0
+        for i in idx:
+            e += _sqdist(pts[i], mean)
+        return e
+
+    def best_split(idx):
+        base = sse(idx)
+        best = None  # (gain, feature, threshold, left, right)
+        for f in range(len(feats[0]) if feats else 0):
+            vals = sorted({feats[i][f] for i in idx})
+            for a, b in zip(vals, vals[1:]):
+                thr = 0.5 * (a + b)
+                left = [i for i in idx if feats[i][f] <= thr]
+                right = [i for i in idx if feats[i][f] > thr]
+                gain = base - sse(left) - sse(right)
+                if best is None or gain > best[0]:
+                    best = (gain, f, thr, left, right)
+        return best
+
+    leaves = [list(range(len(pts)))]
+    while len(leaves) < k:
+        cand = None
+        for li, idx in enumerate(leaves):
+            b = best_split(idx)
+            if b is not None and b[0] > 0.0 and (cand is None or b[0] > cand[0][0]):
+                cand = (b, li)
+        if cand is None:
+            break
+        (gain, f, thr, left, right), li = cand
+        leaves[li:li + 1] = [left, right]
+    out = []
+    for idx in leaves:
+        mean = [0.0] * dim
+        for i in idx:
+            for v in range(dim):
+                mean[v] += pts[i][v]
+        out.append((idx, _argmax_first(mean)))
+    return sorted({v for _, v in out}), out

@@ -43,10 +43,20 @@ struct ManifestEntry {
     int variant;  // registry id
 };
 
+// Node of a regression-tree selector: internal nodes test feature
+// (0: log2 M, 1: log2 N, 2: log2 K) <= threshold; leaves name a variant.
+struct ManifestNode {
+    int feature = -1;
+    double threshold = 0;
+    int left = -1, right = -1;
+    int variant = -1;
+};
+
 struct Manifest {
     std::string method;
     std::vector<int> kappa;  // registry ids, in manifest order
     std::vector<ManifestEntry> map;
+    std::vector<ManifestNode> tree;  // optional; shapes outside the map descend it
     double train_geomean = 0;
 };
 

@@ -9,6 +9,7 @@
 // performance relative to its Oracle), Section V-D (post-processing relative
 // to the best variant per input), Fig. 1 (runtime inference).
 #include <algorithm>
+#include <array>
 #include <cerrno>
 #include <cmath>
 #include <cstdio>
@@ -355,6 +356,225 @@ void select_greedy_swap(const Problem &p, int k, uint64_t seed, std::vector<int>
 
 double log_binom(int n, int k) { return std::lgamma(n + 1.0) - std::lgamma(k + 1.0) - std::lgamma(n - k + 1.0); }
 
+// ---- alternative selections (Section IV-C) ------------------------------------------
+// Points: the training shapes' performance vectors over the candidates,
+// perf = t_best / t (0 where invalid).
+std::vector<std::vector<double>> perf_points(const Table &t, const std::vector<int> &shapes, const Problem &p) {
+    const std::vector<double> tb = best_per_shape(t);
+    std::vector<std::vector<double>> pts(shapes.size(), std::vector<double>(p.cand.size(), 0.0));
+    for (size_t j = 0; j < shapes.size(); ++j)
+        for (size_t c = 0; c < p.cand.size(); ++c) {
+            const double tv = t.t[p.cand[c]][shapes[j]];
+            if (std::isfinite(tv)) pts[j][c] = tb[shapes[j]] / tv;
+        }
+    return pts;
+}
+
+double sqdist(const std::vector<double> &a, const std::vector<double> &b) {
+    double d = 0.0;
+    for (size_t i = 0; i < a.size(); ++i) d += (a[i] - b[i]) * (a[i] - b[i]);
+    return d;
+}
+
+int argmax_first(const std::vector<double> &v) {
+    int best = 0;
+    for (int i = 1; i < (int)v.size(); ++i)
+        if (v[i] > v[best]) best = i;
+    return best;
+}
+
+double splitmix_u(uint64_t seed, uint64_t i) { return (double)(splitmix(seed, i) >> 11) * 0x1.0p-53; }
+
+// k-means (Section IV-C-2): k-means++ initialisation with SplitMix64 draws,
+// Lloyd iterations (nearest centroid, ties to the lower; an empty cluster
+// keeps its centroid) until no assignment changes or 100 rounds; each
+// centroid contributes its highest-performing candidate.
+void select_kmeans(const Table &t, const std::vector<int> &shapes, const Problem &p, int k, uint64_t seed,
+                   std::vector<int> *out) {
+    const std::vector<std::vector<double>> pts = perf_points(t, shapes, p);
+    const int n = (int)pts.size();
+    if (k > n) k = n;
+    uint64_t draws = 0;
+    std::vector<int> chosen;
+    std::vector<std::vector<double>> centers;
+    const int first = (int)(splitmix_u(seed, draws++) * n);
+    chosen.push_back(first);
+    centers.push_back(pts[first]);
+    while ((int)centers.size() < k) {
+        std::vector<double> d2(n);
+        double total = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double m = sqdist(pts[i], centers[0]);
+            for (size_t c = 1; c < centers.size(); ++c) m = std::min(m, sqdist(pts[i], centers[c]));
+            d2[i] = m;
+        }
+        for (int i = 0; i < n; ++i) total += d2[i];
+        int nxt = n - 1;
+        if (total <= 0.0) {
+            for (int i = 0; i < n; ++i)
+                if (std::find(chosen.begin(), chosen.end(), i) == chosen.end()) {
+                    nxt = i;
+                    break;
+                }
+        } else {
+            const double u = splitmix_u(seed, draws) * total;
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                acc += d2[i];
+                if (acc > u) {
+                    nxt = i;
+                    break;
+                }
+            }
+        }
+        ++draws;
+        chosen.push_back(nxt);
+        centers.push_back(pts[nxt]);
+    }
+    std::vector<int> assign(n, -1);
+    for (int iter = 0; iter < 100; ++iter) {
+        bool changed = false;
+        for (int i = 0; i < n; ++i) {
+            int best = 0;
+            double bd = sqdist(pts[i], centers[0]);
+            for (int c = 1; c < (int)centers.size(); ++c) {
+                const double d = sqdist(pts[i], centers[c]);
+                if (d < bd) {
+                    best = c;
+                    bd = d;
+                }
+            }
+            if (assign[i] != best) {
+                assign[i] = best;
+                changed = true;
+            }
+        }
+        if (!changed) break;
+        for (int c = 0; c < (int)centers.size(); ++c) {
+            std::vector<double> mean(p.cand.size(), 0.0);
+            int cnt = 0;
+            for (int i = 0; i < n; ++i)
+                if (assign[i] == c) {
+                    for (size_t v = 0; v < mean.size(); ++v) mean[v] += pts[i][v];
+                    ++cnt;
+                }
+            if (cnt) {
+                for (double &x : mean) x /= cnt;
+                centers[c] = mean;
+            }
+        }
+    }
+    out->clear();
+    for (const auto &c : centers) {
+        const int v = argmax_first(c);
+        if (std::find(out->begin(), out->end(), v) == out->end()) out->push_back(v);
+    }
+    std::sort(out->begin(), out->end());
+}
+
+// Regression tree (Section IV-C-3) from (log2 M, log2 N, log2 K) to the
+// performance vector, squared error summed over the vector, grown best-first
+// to k leaves (ties: lower feature, lower threshold, earlier leaf); each leaf
+// contributes the highest-performing candidate of its mean.
+struct TreeNode {
+    int feature = -1;
+    double threshold = 0;
+    int left = -1, right = -1;
+    int variant = -1;  // leaves: registry id
+};
+
+void select_tree(const Table &t, const std::vector<int> &shapes, const Problem &p, int k, std::vector<int> *out,
+                 std::vector<TreeNode> *tree) {
+    const std::vector<std::vector<double>> pts = perf_points(t, shapes, p);
+    const int n = (int)pts.size();
+    const size_t dim = p.cand.size();
+    std::vector<std::array<double, 3>> feats(n);
+    for (int j = 0; j < n; ++j) {
+        const pt_shape_t &sh = t.shapes[shapes[j]];
+        feats[j] = {std::log2((double)sh.m), std::log2((double)sh.n), std::log2((double)sh.k)};
+    }
+    auto sum_of = [&](const std::vector<int> &idx) {
+        std::vector<double> m(dim, 0.0);
+        for (int i : idx)
+            for (size_t v = 0; v < dim; ++v) m[v] += pts[i][v];
+        return m;
+    };
+    auto sse = [&](const std::vector<int> &idx) {
+        if (idx.empty()) return 0.0;
+        std::vector<double> mean = sum_of(idx);
+        for (double &x : mean) x /= (double)idx.size();
+        double e = 0.0;
+        for (int i : idx) e += sqdist(pts[i], mean);
+        return e;
+    };
+    struct Split {
+        bool ok = false;
+        double gain = 0, thr = 0;
+        int f = -1;
+        std::vector<int> left, right;
+    };
+    auto best_split = [&](const std::vector<int> &idx) {
+        Split best;
+        const double base = sse(idx);
+        for (int f = 0; f < 3; ++f) {
+            std::vector<double> vals;
+            for (int i : idx) vals.push_back(feats[i][f]);
+            std::sort(vals.begin(), vals.end());
+            vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+            for (size_t q = 0; q + 1 < vals.size(); ++q) {
+                const double thr = 0.5 * (vals[q] + vals[q + 1]);
+                std::vector<int> l, r;
+                for (int i : idx) (feats[i][f] <= thr ? l : r).push_back(i);
+                const double gain = base - sse(l) - sse(r);
+                if (!best.ok || gain > best.gain) {
+                    best.ok = true;
+                    best.gain = gain;
+                    best.f = f;
+                    best.thr = thr;
+                    best.left = l;
+                    best.right = r;
+                }
+            }
+        }
+        return best;
+    };
+    std::vector<std::vector<int>> leaves(1);
+    for (int i = 0; i < n; ++i) leaves[0].push_back(i);
+    std::vector<int> leaf_node(1, 0);
+    tree->assign(1, TreeNode());
+    while ((int)leaves.size() < k) {
+        Split cand;
+        int cli = -1;
+        for (int li = 0; li < (int)leaves.size(); ++li) {
+            Split b = best_split(leaves[li]);
+            if (b.ok && b.gain > 0.0 && (cli < 0 || b.gain > cand.gain)) {
+                cand = b;
+                cli = li;
+            }
+        }
+        if (cli < 0) break;
+        const int node = leaf_node[cli];
+        const int ln = (int)tree->size(), rn = ln + 1;
+        tree->push_back(TreeNode());
+        tree->push_back(TreeNode());
+        (*tree)[node].feature = cand.f;
+        (*tree)[node].threshold = cand.thr;
+        (*tree)[node].left = ln;
+        (*tree)[node].right = rn;
+        leaves[cli] = cand.left;
+        leaves.insert(leaves.begin() + cli + 1, cand.right);
+        leaf_node[cli] = ln;
+        leaf_node.insert(leaf_node.begin() + cli + 1, rn);
+    }
+    out->clear();
+    for (size_t li = 0; li < leaves.size(); ++li) {
+        const int c = argmax_first(sum_of(leaves[li]));
+        (*tree)[leaf_node[li]].variant = p.reg[c];
+        if (std::find(out->begin(), out->end(), c) == out->end()) out->push_back(c);
+    }
+    std::sort(out->begin(), out->end());
+}
+
 }  // namespace
 
 // ---- manifest --------------------------------------------------------------------
@@ -366,7 +586,8 @@ static std::string shape_json(const pt_shape_t &s) {
 }
 
 static int write_manifest(const char *path, const char *method, int k, double g, const std::vector<int> &kappa_ids,
-                          const std::vector<std::pair<pt_shape_t, int>> &map) {
+                          const std::vector<std::pair<pt_shape_t, int>> &map,
+                          const std::vector<TreeNode> *tree = nullptr) {
     std::ofstream o(path);
     if (!o) return set_error(PT_EIO, 9, "cannot write manifest '%s'", path);
     auto name = [](int id) {
@@ -383,7 +604,22 @@ static int write_manifest(const char *path, const char *method, int k, double g,
     for (size_t i = 0; i < map.size(); ++i)
         o << (i ? ",\n" : "\n") << "    {" << shape_json(map[i].first)
           << ", \"variant\": " << json::quote(name(map[i].second)) << "}";
-    o << "\n  ]\n}\n";
+    o << "\n  ]";
+    if (tree && !tree->empty()) {
+        // Regression tree over (log2 M, log2 N, log2 K); node 0 is the root.
+        o << ",\n  \"tree\": [";
+        for (size_t i = 0; i < tree->size(); ++i) {
+            const TreeNode &nd = (*tree)[i];
+            char buf[128];
+            if (nd.feature >= 0)
+                std::snprintf(buf, sizeof(buf), "{\"feature\": %d, \"threshold\": %.17g, \"left\": %d, \"right\": %d}",
+                              nd.feature, nd.threshold, nd.left, nd.right);
+            o << (i ? ",\n" : "\n") << "    " << (nd.feature >= 0 ? std::string(buf)
+                                                           : "{\"variant\": " + json::quote(name(nd.variant)) + "}");
+        }
+        o << "\n  ]";
+    }
+    o << "\n}\n";
     o.flush();
     if (!o) return set_error(PT_EIO, 9, "write failed for '%s'", path);
     return PT_OK;
@@ -439,6 +675,34 @@ int read_manifest(const char *path, Manifest *out) {
             m.map.push_back(me);
         }
     }
+    if (const json::Value *tr = root.get("tree"); tr) {
+        if (tr->kind != json::Value::Array) return set_error(PT_EFORMAT, 1, "manifest: tree is not an array");
+        const int nn = (int)tr->arr.size();
+        for (const auto &e : tr->arr) {
+            ManifestNode nd;
+            if (const json::Value *v = e.get("variant"); v) {
+                if (v->kind != json::Value::String) return set_error(PT_EFORMAT, 1, "manifest: bad tree leaf");
+                nd.variant = pt_variant_by_name(v->str.c_str());
+                if (nd.variant < 0) return set_error(PT_EFORMAT, 1, "manifest: unknown variant '%s'", v->str.c_str());
+            } else {
+                const json::Value *f = e.get("feature"), *th = e.get("threshold"), *l = e.get("left"),
+                                  *r = e.get("right");
+                if (!f || !th || !l || !r || f->kind != json::Value::Number || th->kind != json::Value::Number ||
+                    l->kind != json::Value::Number || r->kind != json::Value::Number || f->num < 0 || f->num > 2 ||
+                    l->num < 1 || l->num >= nn || r->num < 1 || r->num >= nn)
+                    return set_error(PT_EFORMAT, 1, "manifest: bad tree node");
+                nd.feature = (int)f->num;
+                nd.threshold = th->num;
+                nd.left = (int)l->num;
+                nd.right = (int)r->num;
+            }
+            m.tree.push_back(nd);
+        }
+        // Children must come after their parent (no cycles).
+        for (int i = 0; i < nn; ++i)
+            if (m.tree[i].feature >= 0 && (m.tree[i].left <= i || m.tree[i].right <= i))
+                return set_error(PT_EFORMAT, 1, "manifest: tree nodes out of order");
+    }
     *out = std::move(m);
     return PT_OK;
 }
@@ -451,6 +715,13 @@ int manifest_pick(const Manifest &m, const pt_shape_t &s) {
     if (m.map.empty()) return m.kappa[0];
     for (const auto &e : m.map)
         if (same_shape(e.shape, s)) return e.variant;
+    if (!m.tree.empty()) {
+        const double f[3] = {std::log2((double)s.m), std::log2((double)s.n), std::log2((double)s.k)};
+        int node = 0;
+        for (size_t steps = 0; steps <= m.tree.size() && m.tree[node].feature >= 0; ++steps)
+            node = f[m.tree[node].feature] <= m.tree[node].threshold ? m.tree[node].left : m.tree[node].right;
+        if (m.tree[node].variant >= 0) return m.tree[node].variant;
+    }
     bool any_same_trans = false;
     for (const auto &e : m.map)
         any_same_trans = any_same_trans || (e.shape.transA == s.transA && e.shape.transB == s.transB);
@@ -524,6 +795,7 @@ int pt_select(const char *table_path, const int *train_idx, int n_train, int k, 
     if (rc != PT_OK) return rc;
     if (p.cand.empty()) return set_error(PT_EFORMAT, 1, "no variant is valid on the training shapes");
     std::vector<int> set;
+    std::vector<TreeNode> tree;
     double val = 0;
     const char *mname = "exact";
     switch (method) {
@@ -544,6 +816,16 @@ int pt_select(const char *table_path, const int *train_idx, int n_train, int k, 
                 mname = "greedy_swap";
                 select_greedy_swap(p, k, seed, &set, &val);
             }
+            break;
+        case PT_SELECT_KMEANS:
+            mname = "kmeans";
+            select_kmeans(t, shapes, p, k, seed, &set);
+            val = set_value(p, set);
+            break;
+        case PT_SELECT_TREE:
+            mname = "tree";
+            select_tree(t, shapes, p, k, &set, &tree);
+            val = set_value(p, set);
             break;
         default:
             return set_error(PT_EINVAL, 5, "unknown selection method %d", method);
@@ -567,7 +849,7 @@ int pt_select(const char *table_path, const int *train_idx, int n_train, int k, 
             }
             if (best >= 0) map.emplace_back(t.shapes[shapes[j]], best);
         }
-        rc = write_manifest(manifest_path, mname, k, val, ids, map);
+        rc = write_manifest(manifest_path, mname, k, val, ids, map, method == PT_SELECT_TREE ? &tree : nullptr);
         if (rc != PT_OK) return rc;
     }
     return PT_OK;

@@ -250,3 +250,66 @@ def test_table_shape_listing(tmp_path):
     path = str(tmp_path / "t.csv")
     _, shapes = write_table(path, t)
     assert pt.table_shapes(path) == shapes
+
+
+# ---- k-means and regression-tree selection (Section IV-C) against the oracle ----------
+
+def _sweep_like(seed, V, invalid=0.1):
+    sizes = (128, 512, 1024, 4096)
+    shapes = [(m, n, k, "N", "N") for m in sizes for n in sizes for k in sizes[:2]]
+    return random_table(seed, V, len(shapes), invalid=invalid), shapes
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_kmeans_selection_matches_oracle(seed, tmp_path):
+    t, shapes = _sweep_like(500 + seed, 12)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t, shapes=shapes)
+    train = list(range(0, len(shapes), 2))
+    for k in (1, 2, 3, 5):
+        ids, val = pt.select(path, train, k, method=pt.PT_SELECT_KMEANS, seed=seed)
+        want, _ = osel.kmeans_select(t, k, train, seed=seed)
+        assert ids == want, (k, ids, want)
+        assert val == pytest.approx(osel.set_performance(t, want, train), rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_tree_selection_matches_oracle(seed, tmp_path):
+    t, shapes = _sweep_like(600 + seed, 10)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t, shapes=shapes)
+    train = list(range(len(shapes)))
+    feats = [tuple(math.log2(x) for x in sh[:3]) for sh in shapes]
+    for k in (1, 2, 4, 6):
+        ids, val = pt.select(path, train, k, method=pt.PT_SELECT_TREE)
+        want, _ = osel.tree_select(t, k, train, feats)
+        assert ids == want, (k, ids, want)
+
+
+def test_tree_manifest_is_the_runtime_selector_for_unlisted_shapes(tmp_path):
+    t, shapes = _sweep_like(700, 8, invalid=0.0)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t, shapes=shapes)
+    man = str(tmp_path / "tree.json")
+    train = list(range(0, len(shapes), 2))
+    pt.select(path, train, 4, method=pt.PT_SELECT_TREE, manifest=man)
+    m = json.load(open(man))
+    assert m["method"] == "tree" and len(m["tree"]) >= 1
+
+    def descend(q):
+        f = [math.log2(x) for x in q]
+        node = 0
+        while "variant" not in m["tree"][node]:
+            nd = m["tree"][node]
+            node = nd["left"] if f[nd["feature"]] <= nd["threshold"] else nd["right"]
+        return pt.variant_by_name(m["tree"][node]["variant"])
+
+    pt.load_manifest(man)
+    try:
+        for q in [(200, 300, 700), (2048, 96, 4000), (4096, 4096, 4096), (130, 5000, 129)]:
+            assert pt.selected_variant(*q) == descend(q)
+        # Listed (training) shapes keep their fastest member.
+        s = train[3]
+        assert pt.selected_variant(*shapes[s][:3]) == osel.best_in_set(t, [pt.variant_by_name(x) for x in m["kappa"]], s)
+    finally:
+        pt.load_manifest(None)

@@ -138,3 +138,85 @@ def test_nearest_shape_rule():
 def test_best_in_set_ties_go_to_lowest_id():
     t = np.array([[3.0], [1.0], [1.0]])
     assert osel.best_in_set(t, [2, 1, 0], 0) == 1
+
+
+# ---- alternative selections (Section IV-C): k-means and regression tree ---------------
+
+def _feat(shapes):
+    return [tuple(math.log2(x) for x in sh) for sh in shapes]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_kmeans_single_cluster_is_best_mean_performance(seed):
+    t = _random_table(200 + seed, 7, 9, invalid=0.1)
+    ids, assign = osel.kmeans_select(t, 1, range(9), seed=seed)
+    perf = np.where(np.isfinite(t), osel.per_shape_best(t)[None, :] / t, 0.0)
+    assert ids == [int(np.argmax(perf.mean(axis=1)))]
+    assert set(assign) == {0}
+
+
+def test_kmeans_one_cluster_per_shape_recovers_per_shape_best():
+    # Every shape has a different best variant (all points distinct).
+    t = np.full((5, 5), 4.0)
+    for s in range(5):
+        t[s, s] = 1.0
+    t[0, 1] = 2.0
+    ids, _ = osel.kmeans_select(t, 5, range(5), seed=3)
+    assert ids == sorted({osel.autotune(t, s) for s in range(5)}) == [0, 1, 2, 3, 4]
+
+
+def test_kmeans_planted_clusters():
+    # Shapes 0-3 favour variant 2, shapes 4-7 favour variant 5, strongly.
+    rng = np.random.default_rng(0)
+    t = 3.0 + rng.random((6, 8))
+    t[2, :4] = 1.0
+    t[5, 4:] = 1.0
+    for seed in range(5):
+        ids, assign = osel.kmeans_select(t, 2, range(8), seed=seed)
+        assert ids == [2, 5]
+        assert len(set(assign[:4])) == 1 and len(set(assign[4:])) == 1 and assign[0] != assign[4]
+
+
+def test_tree_single_leaf_is_best_mean_performance():
+    t = _random_table(300, 6, 8)
+    shapes = [(2 ** (7 + s % 4), 2 ** (7 + s // 4), 256) for s in range(8)]
+    ids, leaves = osel.tree_select(t, 1, range(8), _feat(shapes))
+    perf = np.where(np.isfinite(t), osel.per_shape_best(t)[None, :] / t, 0.0)
+    assert ids == [int(np.argmax(perf.mean(axis=1)))]
+    assert len(leaves) == 1
+
+
+def test_tree_planted_split_on_m():
+    # M <= 512 -> variant 0 is best, M > 512 -> variant 1; N, K are noise.
+    shapes = [(m, n, k) for m in (128, 512, 1024, 4096) for n in (128, 4096) for k in (256, 2048)]
+    t = np.full((3, len(shapes)), 2.0)
+    for s, (m, n, k) in enumerate(shapes):
+        t[0 if m <= 512 else 1, s] = 1.0
+        t[2, s] = 1.5 + 0.01 * (n == 4096)
+    ids, leaves = osel.tree_select(t, 2, range(len(shapes)), _feat(shapes))
+    assert ids == [0, 1]
+    assert sorted(len(ix) for ix, _ in leaves) == [8, 8]
+    for ix, v in leaves:
+        assert {shapes[i][0] <= 512 for i in ix} == {v == 0}
+
+
+def test_tree_first_split_maximises_error_reduction_by_brute_force():
+    t = _random_table(400, 5, 10, invalid=0.0)
+    feats = [(float(a), float(b)) for a, b in np.random.default_rng(4).integers(0, 5, size=(10, 2))]
+    _, leaves = osel.tree_select(t, 2, range(10), feats)
+    perf = osel.per_shape_best(t)[None, :] / t  # (V, S)
+    pts = perf.T
+
+    def sse(ix):
+        return float(((pts[ix] - pts[ix].mean(axis=0)) ** 2).sum()) if len(ix) else 0.0
+
+    best = None
+    for f in range(2):
+        for thr in sorted({x[f] for x in feats}):
+            left = [i for i in range(10) if feats[i][f] <= thr]
+            right = [i for i in range(10) if feats[i][f] > thr]
+            if left and right:
+                gain = sse(list(range(10))) - sse(left) - sse(right)
+                best = gain if best is None else max(best, gain)
+    got = sse(list(range(10))) - sse(leaves[0][0]) - sse(leaves[1][0])
+    assert got == pytest.approx(best, rel=1e-9)
