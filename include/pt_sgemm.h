@@ -205,7 +205,7 @@ int pt_shutdown(void);
  * array of PT_NOALLOC_SCRATCH_BYTES bytes of device memory that belongs to
  * the library image (every GPU that loads the library holds it until the
  * process exits).  It calls no cudaMalloc, cudaFree or allocating routine.
- * Limit: 2 * (M + N) * round_up(K, 4) * 4 bytes (plus up to 1 KiB of
+ * Limit: 2 * (M + N) * round_up(K, 8) * 4 bytes (plus up to 1 KiB of
  * alignment) must not exceed PT_NOALLOC_SCRATCH_BYTES, else PT_EINVAL and
  * nothing is launched.  The first call on a device looks up the array's
  * device address on that device (the device must be current) and sets the

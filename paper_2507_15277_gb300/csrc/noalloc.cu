@@ -117,14 +117,14 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
         return set_error(PT_EUNSUPPORTED, 3, "shape too large for the grid");
 
     // Two TF32 planes (hi, lo) of op(A) (M rows) and of op(B)^T (N rows), K-major,
-    // row pitch rounded up to 4 floats, each plane 256-byte aligned.
-    const int64_t pitch = (K + 3) / 4 * 4;
+    // row pitch rounded up to 8 floats, each plane 256-byte aligned.
+    const int64_t pitch = (K + 7) / 8 * 8;
     const int64_t a_plane = align256(M * pitch * 4);
     const int64_t b_plane = align256(N * pitch * 4);
     const int64_t need = 2 * (a_plane + b_plane);
     if (need > (int64_t)PT_NOALLOC_SCRATCH_BYTES)
         return set_error(PT_EINVAL, 0,
-                         "M=%lld N=%lld K=%lld needs %lld bytes of scratch (2 planes x (M + N) x round_up(K, 4) x 4 "
+                         "M=%lld N=%lld K=%lld needs %lld bytes of scratch (2 planes x (M + N) x round_up(K, 8) x 4 "
                          "bytes); the allocation-free entry point has %lld",
                          (long long)M, (long long)N, (long long)K, (long long)need,
                          (long long)PT_NOALLOC_SCRATCH_BYTES);
@@ -146,11 +146,12 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     // left in the array by an earlier call is used.
     unsigned char *wA = ws;
     unsigned char *wB = ws + 2 * a_plane;
-    const dim3 blk(32, 8);
-    tc_split_kernel<kTcTf32><<<dim3((unsigned)((K + 31) / 32), (unsigned)((M + 31) / 32)), blk, 0, st>>>(
-        A, lda, ta, (int)M, (int)K, wA, a_plane, pitch);
-    tc_split_kernel<kTcTf32><<<dim3((unsigned)((K + 31) / 32), (unsigned)((N + 31) / 32)), blk, 0, st>>>(
-        B, ldb, tb ? 0 : 1, (int)N, (int)K, wB, b_plane, pitch);
+    const int va = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
+    const int vb = (reinterpret_cast<uintptr_t>(B) % 16 == 0 && ldb % 4 == 0) ? 1 : 0;
+    tc_split_kernel<kTcTf32><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)((M + 31) / 32)), 256, 0, st>>>(
+        A, lda, ta, (int)M, (int)K, wA, a_plane, pitch, va);
+    tc_split_kernel<kTcTf32><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)((N + 31) / 32)), 256, 0, st>>>(
+        B, ldb, tb ? 0 : 1, (int)N, (int)K, wB, b_plane, pitch, vb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 

@@ -72,7 +72,9 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int64_t gy = ((int64_t)a.M + V::BM - 1) / V::BM;
     if (gy > 65535 || ((int64_t)a.M + 31) / 32 > 65535 || ((int64_t)a.N + 31) / 32 > 65535)
         return set_error(PT_EUNSUPPORTED, 3, "shape too large for this variant's grid");
-    const int64_t pitch = ((int64_t)a.K + (16 / V::ELEM) - 1) / (16 / V::ELEM) * (16 / V::ELEM);
+    // Row pitch: a multiple of 8 elements (16-byte aligned rows, whole
+    // 8-column groups for the split kernel's vector stores).
+    const int64_t pitch = ((int64_t)a.K + 7) / 8 * 8;
     const int64_t a_plane = align256((int64_t)a.M * pitch * V::ELEM);
     const int64_t b_plane = align256((int64_t)a.N * pitch * V::ELEM);
     const size_t need = (size_t)V::P * (size_t)(a_plane + b_plane);
@@ -92,11 +94,12 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
 
     unsigned char *wA = static_cast<unsigned char *>(ws);
     unsigned char *wB = wA + V::P * a_plane;
-    const dim3 blk(32, 8);
-    tc_split_kernel<V::KIND><<<dim3((unsigned)((a.K + 31) / 32), (unsigned)((a.M + 31) / 32)), blk, 0, st>>>(
-        a.A, a.lda, a.ta, a.M, a.K, wA, a_plane, pitch);
-    tc_split_kernel<V::KIND><<<dim3((unsigned)((a.K + 31) / 32), (unsigned)((a.N + 31) / 32)), blk, 0, st>>>(
-        a.B, a.ldb, a.tb ? 0 : 1, a.N, a.K, wB, b_plane, pitch);
+    const int va = (!misaligned(a.A, 16) && a.lda % 4 == 0) ? 1 : 0;
+    const int vb = (!misaligned(a.B, 16) && a.ldb % 4 == 0) ? 1 : 0;
+    tc_split_kernel<V::KIND><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)((a.M + 31) / 32)), 256, 0, st>>>(
+        a.A, a.lda, a.ta, a.M, a.K, wA, a_plane, pitch, va);
+    tc_split_kernel<V::KIND><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)((a.N + 31) / 32)), 256, 0, st>>>(
+        a.B, a.ldb, a.tb ? 0 : 1, a.N, a.K, wB, b_plane, pitch, vb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 

@@ -119,60 +119,101 @@ __device__ __forceinline__ uint16_t bf16_rne_bits(float x) {
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
 
-// Writes the planes of element (r, k) (r < rows, k < K).
+// Planes of 8 consecutive elements x[0..8) of row r starting at column k
+// (k a multiple of 8, k + 8 <= pitch): one 16-byte store per plane for BF16,
+// two per plane for TF32.  Elements at or beyond K are written as zero.
 template <int KIND>
-__device__ __forceinline__ void split_store(unsigned char *ws, int64_t plane_bytes, int64_t pitch, int r, int k,
-                                            float x) {
+__device__ __forceinline__ void split_store8(unsigned char *ws, int64_t plane_bytes, int64_t pitch, int r, int k,
+                                             const float (&x)[8]) {
+    const int64_t off = (int64_t)r * pitch + k;
     if constexpr (KIND == kTcTf32) {
-        float *p = reinterpret_cast<float *>(ws) + (int64_t)r * pitch + k;
-        const float hi = tf32_rne(x);
-        const float lo = tf32_rne(x - hi);
-        p[0] = hi;
-        reinterpret_cast<float *>(ws + plane_bytes)[(int64_t)r * pitch + k] = lo;
+        float hi[8], lo[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            hi[i] = tf32_rne(x[i]);
+            lo[i] = tf32_rne(x[i] - hi[i]);
+        }
+        float4 *ph = reinterpret_cast<float4 *>(reinterpret_cast<float *>(ws) + off);
+        float4 *pl = reinterpret_cast<float4 *>(reinterpret_cast<float *>(ws + plane_bytes) + off);
+        ph[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        ph[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
+        pl[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        pl[1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
     } else {
-        const uint16_t b0 = bf16_rne_bits(x);
-        const float r1 = x - bf16_to_f32(b0);
-        const uint16_t b1 = bf16_rne_bits(r1);
-        const float r2 = r1 - bf16_to_f32(b1);
-        const uint16_t b2 = bf16_rne_bits(r2);
-        const int64_t off = (int64_t)r * pitch + k;
-        reinterpret_cast<uint16_t *>(ws)[off] = b0;
-        reinterpret_cast<uint16_t *>(ws + plane_bytes)[off] = b1;
-        reinterpret_cast<uint16_t *>(ws + 2 * plane_bytes)[off] = b2;
+        uint32_t b[3][4];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            uint16_t q[3][2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float v = x[i + j];
+                q[0][j] = bf16_rne_bits(v);
+                const float r1 = v - bf16_to_f32(q[0][j]);
+                q[1][j] = bf16_rne_bits(r1);
+                q[2][j] = bf16_rne_bits(r1 - bf16_to_f32(q[1][j]));
+            }
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl) b[pl][i / 2] = (uint32_t)q[pl][0] | ((uint32_t)q[pl][1] << 16);
+        }
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl)
+            *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(ws + pl * plane_bytes) + off) =
+                make_uint4(b[pl][0], b[pl][1], b[pl][2], b[pl][3]);
     }
 }
 
-// Split of a logical rows x K operand X(r, k) into K-major planes.
+// Split of a logical rows x K operand X(r, k) into K-major planes with row
+// pitch `pitch` (a multiple of 8 elements, >= round_up(K, 8)); the padding
+// columns [K, pitch) are written as zero.
 // trans == 0: X(r, k) at src[r*ld + k];  trans == 1: X(r, k) at src[k*ld + r].
-// 32 x 32 tiles through shared memory so both the read and the write are
-// coalesced.  Block (32, 8).
+// A block of 256 threads covers 32 rows x 64 columns; every thread writes 8
+// consecutive columns of one row with 16-byte stores.  The transposed case
+// goes through shared memory so that the global reads run along r.
+// vec4: src and ld allow 16-byte loads along the contiguous direction.
 template <int KIND>
 __global__ void __launch_bounds__(256) tc_split_kernel(const float *__restrict__ src, int64_t ld, int trans,
                                                        int rows, int K, unsigned char *ws, int64_t plane_bytes,
-                                                       int64_t pitch) {
-    __shared__ float tile[32][33];
-    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+                                                       int64_t pitch, int vec4) {
+    __shared__ float tile[64][33];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+    const int tid = threadIdx.x;
+    const int r = r0 + (tid >> 3), k = k0 + (tid & 7) * 8;
+    float x[8];
     if (trans) {
-        // read along r (contiguous), tile[k][r]
+        // tile[kk][rr] <- X(r0 + rr, k0 + kk) = src[(k0 + kk) * ld + r0 + rr]
 #pragma unroll
-        for (int j = 0; j < 32; j += 8) {
-            const int k = k0 + ty + j, r = r0 + tx;
-            tile[ty + j][tx] = (k < K && r < rows) ? src[(int64_t)k * ld + r] : 0.f;
+        for (int j = 0; j < 2; ++j) {
+            const int kk = (tid >> 3) + 32 * j, rr = (tid & 7) * 4;
+            const int gk = k0 + kk, gr = r0 + rr;
+            const float *p = src + (int64_t)gk * ld + gr;
+            float v[4];
+            if (gk < K && gr + 3 < rows && vec4) {
+                const float4 q = *reinterpret_cast<const float4 *>(p);
+                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = (gk < K && gr + i < rows) ? p[i] : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tile[kk][rr + i] = v[i];
         }
         __syncthreads();
+        const int rr = tid >> 3, kk = (tid & 7) * 8;
 #pragma unroll
-        for (int j = 0; j < 32; j += 8) {
-            const int r = r0 + ty + j, k = k0 + tx;
-            if (r < rows && k < K) split_store<KIND>(ws, plane_bytes, pitch, r, k, tile[tx][ty + j]);
-        }
+        for (int i = 0; i < 8; ++i) x[i] = tile[kk + i][rr];
     } else {
+        const float *p = src + (int64_t)r * ld + k;
+        if (r < rows && k + 7 < K && vec4) {
+            const float4 q0 = *reinterpret_cast<const float4 *>(p);
+            const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
+            x[0] = q0.x; x[1] = q0.y; x[2] = q0.z; x[3] = q0.w;
+            x[4] = q1.x; x[5] = q1.y; x[6] = q1.z; x[7] = q1.w;
+        } else {
 #pragma unroll
-        for (int j = 0; j < 32; j += 8) {
-            const int r = r0 + ty + j, k = k0 + tx;
-            if (r < rows && k < K) split_store<KIND>(ws, plane_bytes, pitch, r, k, src[(int64_t)r * ld + k]);
+            for (int i = 0; i < 8; ++i) x[i] = (r < rows && k + i < K) ? p[i] : 0.f;
         }
     }
+    if (r < rows && k < pitch) split_store8<KIND>(ws, plane_bytes, pitch, r, k, x);
 }
 
 struct TcArgs {
