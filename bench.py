@@ -55,9 +55,85 @@ def parse():
     p.add_argument("--single", default=None, metavar="M,N,K",
                    help="profiling mode: run one variant (--variant) on one shape, no tuning")
     p.add_argument("--variant", default=None, help="variant name for --single")
-    p.add_argument("--report", default=None, choices=["splitprec"],
-                   help="splitprec: tensor-core split-precision vs FP32 SIMT on the split-precision shapes")
+    p.add_argument("--report", default=None, choices=["splitprec", "grouped"],
+                   help="splitprec: tensor-core split-precision vs FP32 SIMT on the split-precision shapes; "
+                        "grouped: 512 uneven problems, persistent grouped launch vs separate launches")
     return p.parse_args()
+
+
+def report_grouped(args):
+    """512 independent problems (M, N, K = 8*round(2^U[5,11]/8), clamped to
+    [32, 2048], seed 5; entries U[-1,1]): one persistent grouped launch with
+    per-problem tiles from the k = 8 selector, against 512 separate launches
+    of the single best variant (k = 1) and 512 pt_sgemm calls through the
+    k = 8 selector.  Every arm is captured once as a CUDA graph and replayed;
+    CUDA-event time over the replays."""
+    import torch
+
+    import paper_2507_15277_gb300 as pt
+    from workloads import grouped_problems, matrix, parity_split, sweep_shapes
+    dev = torch.device("cuda", 0)
+    out_dir = args.out_dir or tempfile.mkdtemp(prefix="ptgrouped_")
+    os.makedirs(out_dir, exist_ok=True)
+    table = args.table or os.path.join(out_dir, "table.csv")
+    if not args.table:
+        pt.tune(sweep_shapes(), table, reps_min=5, reps_max=args.tune_reps_max, target_ms=args.tune_target_ms)
+    train, _ = parity_split()
+    m1, m8 = os.path.join(out_dir, "grouped_k1.json"), os.path.join(out_dir, "grouped_k8.json")
+    ids1, _ = pt.select(table, train, 1, manifest=m1)
+    pt.select(table, train, 8, manifest=m8)
+    probs = grouped_problems()
+    items = []
+    for i, (M, N, K) in enumerate(probs):
+        A = torch.from_numpy(matrix("uniform", 5000 + i, M, K)).to(dev)
+        B = torch.from_numpy(matrix("uniform", 6000 + i, K, N)).to(dev)
+        items.append((A, B, torch.empty((M, N), device=dev), "N", "N", 1.0, 0.0))
+    flops = sum(2.0 * M * N * K for (M, N, K) in probs)
+    pt.load_manifest(m8)
+    arr = pt.grouped_problems(items)
+    ddesc = pt.upload_problems(arr, dev)
+    tiles = {}
+    for i in range(len(items)):
+        tiles[arr[i].tile] = tiles.get(arr[i].tile, 0) + 1
+    stream = torch.cuda.Stream(dev)
+
+    def arm_single():
+        for (A, B, C, *_r) in items:
+            pt.sgemm(A, B, C, variant=ids1[0], stream=stream)
+
+    def arm_selector():
+        for (A, B, C, *_r) in items:
+            pt.sgemm(A, B, C, stream=stream)
+
+    def arm_grouped():
+        pt.sgemm_grouped(arr, ddesc=ddesc, stream=stream, device=dev)
+
+    res = {}
+    reps = max(3, args.steps // 10)
+    for name, fn in (("single_best_512_launches", arm_single), ("selector_512_launches", arm_selector),
+                     ("grouped_persistent_1_launch", arm_grouped)):
+        with torch.cuda.stream(stream):
+            fn()  # warm: attributes, workspaces
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                fn()
+            for _ in range(3):
+                g.replay()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(stream)
+            stream.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+        del g
+    pt.load_manifest(None)
+    print(json.dumps({"mode": "grouped", "problems": len(probs), "gflop": flops / 1e9,
+                      "single_best_variant": pt.variant(ids1[0])["name"], "tiles_used": tiles,
+                      "replays": reps, "arms": res}))
+    return 0
 
 
 def report_splitprec(args):
@@ -307,6 +383,8 @@ def main():
         return single(args)
     if args.report == "splitprec":
         return report_splitprec(args)
+    if args.report == "grouped":
+        return report_grouped(args)
 
     import numpy as np
     import torch

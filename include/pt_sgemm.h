@@ -187,6 +187,43 @@ int pt_selected_variant(char transA, char transB, int64_t M, int64_t N, int64_t 
                         const float *A, int64_t lda, const float *B, int64_t ldb,
                         const float *C, int64_t ldc);
 
+/* ---- grouped SGEMM: many independent problems in one persistent launch ----
+ * (The paper tunes single GEMM calls; this batches uneven problems, each
+ * with its own variant choice.)  One descriptor per problem; same operation
+ * and conventions as pt_sgemm per problem.  `tile` is the problem's tile
+ * configuration in the grouped kernel (0: 64x64, 1: 128x64, 2: 128x128 with
+ * 16-byte aligned A, B, C and leading dimensions divisible by 4; 3: 64x64
+ * for any alignment); pt_grouped_plan fills it from the runtime selector. */
+typedef struct pt_gemm_problem {
+    int64_t m, n, k;
+    const float *A;
+    int64_t lda;
+    const float *B;
+    int64_t ldb;
+    float *C;
+    int64_t ldc;
+    float alpha, beta;
+    char transA, transB;
+    int16_t reserved;
+    int32_t tile;
+} pt_gemm_problem_t;
+
+#define PT_GROUPED_MAX 4096  /* problems per pt_sgemm_grouped call */
+
+/* Sets problems[i].tile for every problem (host array): the variant the
+ * loaded manifest's selector picks for that shape (see pt_sgemm) mapped to
+ * the grouped tile of the nearest area (tensor-core picks -> 128x128); 3
+ * when the problem's operands are not 16-byte aligned. */
+int pt_grouped_plan(pt_gemm_problem_t *problems, int count);
+
+/* Runs `count` problems in one launch of a persistent kernel (a grid of
+ * resident CTAs walking all problems' tiles).  `problems` (host) is validated;
+ * `problems_dev` must be a device copy of the same array, caller-owned, left
+ * unchanged until the launch has completed.  Asynchronous on `stream`; no
+ * workspace and no allocation. */
+int pt_sgemm_grouped(const pt_gemm_problem_t *problems, const pt_gemm_problem_t *problems_dev, int count,
+                     void *stream);
+
 /* Frees the library's device workspaces (the split planes of the tensor-core
  * variants, one buffer per device and stream, grown on first use of a larger
  * shape; growing is refused with PT_EUNSUPPORTED while the stream is being

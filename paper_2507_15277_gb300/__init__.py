@@ -25,6 +25,7 @@ from ._lib import (PT_LOADER_CPASYNC, PT_LOADER_TMA, PT_SCORE_BEST_OF_SET,  # no
 __all__ = [
     "sgemm", "reference", "num_variants", "variant", "variants", "variant_by_name", "default_variant",
     "tune", "select", "score", "table_shapes", "load_manifest", "selected_variant", "device_status",
+    "grouped_problems", "upload_problems", "sgemm_grouped",
     "PtError",
 ]
 
@@ -202,6 +203,41 @@ def table_shapes(table_path: str) -> list:
         _lib.check(_l().pt_table_shape(table_path.encode(), i, ctypes.byref(s)), "pt_table_shape")
         out.append((s.m, s.n, s.k, s.transA.decode(), s.transB.decode()))
     return out
+
+
+def grouped_problems(items, plan: bool = True):
+    """Descriptor array for pt_sgemm_grouped from (A, B, C, transA, transB,
+    alpha, beta) tuples of CUDA tensors; tiles from the runtime selector."""
+    arr = (_lib.Problem * len(items))()
+    for i, (A, B, C, ta, tb, alpha, beta) in enumerate(items):
+        M, N, K = _dims(A, B, ta, tb)
+        arr[i] = _lib.Problem(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
+                              float(alpha), float(beta), ta.encode(), tb.encode(), 0, 3)
+    if plan:
+        _lib.check(_l().pt_grouped_plan(arr, len(items)), "pt_grouped_plan")
+    return arr
+
+
+def upload_problems(arr, device=None):
+    """Device copy of a descriptor array (a uint8 CUDA tensor)."""
+    import torch
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    return torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(dev)
+
+
+def sgemm_grouped(arr, ddesc=None, stream=None, device=None):
+    """One persistent launch over a descriptor array (see grouped_problems).
+    ``ddesc`` is its device copy (upload_problems); made here when omitted.
+    Returns the device copy; keep it alive and unchanged until the launch has
+    completed (for a captured CUDA graph: as long as the graph is replayed)."""
+    import torch
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    if ddesc is None:
+        ddesc = upload_problems(arr, dev)
+    with torch.cuda.device(dev):
+        _lib.check(_l().pt_sgemm_grouped(arr, ctypes.c_void_p(ddesc.data_ptr()), len(arr), _stream(stream, dev)),
+                   "pt_sgemm_grouped")
+    return ddesc
 
 
 def load_manifest(path: str | None) -> None:

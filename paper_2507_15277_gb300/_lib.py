@@ -56,6 +56,13 @@ class TuneOpts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("pool_bytes", _i64), ("verbose", ctypes.c_int)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("m", _i64), ("n", _i64), ("k", _i64), ("A", _p), ("lda", _i64), ("B", _p), ("ldb", _i64),
+                ("C", _p), ("ldc", _i64), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("transA", ctypes.c_char), ("transB", ctypes.c_char), ("reserved", ctypes.c_int16),
+                ("tile", ctypes.c_int32)]
+
+
 _GEMM_ARGS = [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, ctypes.c_float, _p, _i64, _p, _i64,
               ctypes.c_float, _p, _i64, _p]
 
@@ -87,6 +94,8 @@ SIGNATURES = {
     "pt_device_status": (ctypes.c_int, []),
     "pt_shutdown": (ctypes.c_int, []),
     "pt_sgemm_3xtf32_noalloc": (ctypes.c_int, _GEMM_ARGS),
+    "pt_grouped_plan": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int]),
+    "pt_sgemm_grouped": (ctypes.c_int, [ctypes.POINTER(Problem), _p, ctypes.c_int, _p]),
 }
 
 _lib = None

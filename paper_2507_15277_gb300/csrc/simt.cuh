@@ -220,11 +220,14 @@ __device__ __forceinline__ void store4(float *__restrict__ c, float4 v, int ncol
     }
 }
 
-// ---- the kernel --------------------------------------------------------------
+// ---- one CTA tile -------------------------------------------------------------
+// Computes the BM x BN tile at (m0, n0) of C (over k-tiles of split kz when
+// SPLITK > 1).  Shared by the per-GEMM kernel below and the persistent
+// grouped kernel (which calls it for successive tiles; it leaves shared
+// memory free for the next call).
 template <class V>
-__global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
-    simt_sgemm_kernel(const GemmArgs args, const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB) {
+__device__ __forceinline__ void simt_body(const GemmArgs &args, const CUtensorMap *tmA, const CUtensorMap *tmB,
+                                          const int m0, const int n0, const int kz) {
     constexpr int BM = V::BM, BN = V::BN, BK = V::BK, TM = V::TM, TN = V::TN, KL = V::KL;
     constexpr int STAGES = V::STAGES, THREADS = V::THREADS, LM = V::LM, LN = V::LN;
     constexpr bool TMA = V::LOADER == kLoaderTma;
@@ -249,14 +252,13 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
     const int wn0 = (warp % V::WARPS_N) * V::WN;
 
     const int M = args.M, N = args.N, K = args.K;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
 
     // K range of this CTA (split-K across the cluster's z dimension).
     const int kt_total = (K + BK - 1) / BK;
     int kt_begin = 0, nkt = kt_total;
     if constexpr (V::SPLITK > 1) {
         const int per = (kt_total + V::SPLITK - 1) / V::SPLITK;
-        kt_begin = (int)blockIdx.z * per;
+        kt_begin = kz * per;
         const int kt_end = kt_begin + per < kt_total ? kt_begin + per : kt_total;
         nkt = kt_end > kt_begin ? kt_end - kt_begin : 0;
     }
@@ -282,9 +284,9 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
         if constexpr (TMA) {
             const uint32_t bar = bar0 + 8 * s;
             mbar_arrive_expect_tx(bar, (uint32_t)((BM * BK + BK * BN) * 4));
-            if constexpr (AKM) tma_load_2d(dA, &tmA, bar, k0, m0);
-            else tma_load_2d(dA, &tmA, bar, m0, k0);
-            tma_load_2d(dB, &tmB, bar, n0, k0);
+            if constexpr (AKM) tma_load_2d(dA, tmA, bar, k0, m0);
+            else tma_load_2d(dA, tmA, bar, m0, k0);
+            tma_load_2d(dB, tmB, bar, n0, k0);
         } else {
             if constexpr (AKM) {
                 copy_direct<THREADS, BM, BK, V::VEC, BK, true, V::SW_MASK>(dA, args.A, args.lda, m0, k0, M, K, tid);
@@ -381,8 +383,8 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
         // normally already satisfied.
         const uint32_t emp0 = bar0 + 8 * STAGES;
         if (tid == 0) {
-            prefetch_tensormap(&tmA);
-            prefetch_tensormap(&tmB);
+            prefetch_tensormap(tmA);
+            prefetch_tensormap(tmB);
 #pragma unroll
             for (int s = 0; s < STAGES; ++s) {
                 mbar_init(bar0 + 8 * s, 1);
@@ -528,6 +530,13 @@ __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
         }
         cluster_sync();  // no CTA leaves while a peer may still read its tile
     }
+}
+
+template <class V>
+__global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
+    simt_sgemm_kernel(const GemmArgs args, const __grid_constant__ CUtensorMap tmA,
+                      const __grid_constant__ CUtensorMap tmB) {
+    simt_body<V>(args, &tmA, &tmB, (int)blockIdx.y * V::BM, (int)blockIdx.x * V::BN, (int)blockIdx.z);
 }
 
 }  // namespace pt
