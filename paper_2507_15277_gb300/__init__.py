@@ -71,6 +71,8 @@ def _ld(t):
     import torch
     if t.dtype != torch.float32:
         raise TypeError("float32 tensors only")
+    if t.numel() == 0:
+        return max(int(t.shape[1]), 1)
     if t.shape[1] > 1 and t.stride(1) != 1:
         raise ValueError("row-major storage with unit column stride required")
     return max(int(t.stride(0)), int(t.shape[1]), 1) if t.shape[0] > 1 else max(int(t.shape[1]), 1)
