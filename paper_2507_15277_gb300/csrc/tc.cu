@@ -69,8 +69,8 @@ inline int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 
 template <class V>
 int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
-    const int64_t gy = ((int64_t)a.M + V::BM - 1) / V::BM;
-    if (gy > 65535 || ((int64_t)a.M + 31) / 32 > 65535 || ((int64_t)a.N + 31) / 32 > 65535)
+    const int64_t tiles = (((int64_t)a.M + V::BM - 1) / V::BM) * (((int64_t)a.N + V::BN - 1) / V::BN);
+    if (tiles > 0x7fffffff || ((int64_t)a.M + 31) / 32 > 65535 || ((int64_t)a.N + 31) / 32 > 65535)
         return set_error(PT_EUNSUPPORTED, 3, "shape too large for this variant's grid");
     // Row pitch: a multiple of 8 elements (16-byte aligned rows, whole
     // 8-column groups for the split kernel's vector stores).
@@ -121,9 +121,22 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     t.beta = a.beta;
     t.vec4 = (!misaligned(a.C, 16) && a.ldc % 4 == 0) ? 1 : 0;
     t.err = a.err;
-    const dim3 grid((unsigned)((a.N + V::BN - 1) / V::BN), (unsigned)gy);
-    tc_sgemm_kernel<V><<<grid, V::THREADS, V::SMEM_BYTES, st>>>(t, mA, mB);
-    e = cudaGetLastError();
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)tiles, 1, V::SPLITK);
+    cfg.blockDim = dim3(V::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = V::SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (V::SPLITK > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = V::SPLITK;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    e = cudaLaunchKernelEx(&cfg, tc_sgemm_kernel<V>, t, mA, mB);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "tensor-core kernel: %s", cudaGetErrorString(e));
     return PT_OK;
 }
@@ -138,7 +151,7 @@ VariantEntry tc_entry(const char *name) {
     v.desc.kl = 1;
     v.desc.vec = 1;
     v.desc.stages = V::STAGES;
-    v.desc.splitk = 1;
+    v.desc.splitk = V::SPLITK;
     v.desc.loader = PT_LOADER_TMA;
     v.desc.a_kmajor = 1;
     v.desc.threads = V::THREADS;
@@ -160,6 +173,16 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcTf32, 64, 4>>("tc3xtf32_m128n64_p4"),
         tc_entry<Tc<kTcBf16x3, 128, 2>>("tcbf16x3_m128n128_p2"),
         tc_entry<Tc<kTcBf16x3, 64, 3>>("tcbf16x3_m128n64_p3"),
+        tc_entry<Tc<kTcTf32, 128, 3, 2>>("tc3xtf32_m128n128_p3_sk2"),
+        tc_entry<Tc<kTcTf32, 128, 3, 4>>("tc3xtf32_m128n128_p3_sk4"),
+        tc_entry<Tc<kTcTf32, 64, 4, 2>>("tc3xtf32_m128n64_p4_sk2"),
+        tc_entry<Tc<kTcTf32, 64, 4, 4>>("tc3xtf32_m128n64_p4_sk4"),
+        tc_entry<Tc<kTcTf32, 64, 4, 8>>("tc3xtf32_m128n64_p4_sk8"),
+        tc_entry<Tc<kTcBf16x3, 128, 2, 2>>("tcbf16x3_m128n128_p2_sk2"),
+        tc_entry<Tc<kTcBf16x3, 128, 2, 4>>("tcbf16x3_m128n128_p2_sk4"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 2>>("tcbf16x3_m128n64_p3_sk2"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 4>>("tcbf16x3_m128n64_p3_sk4"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 8>>("tcbf16x3_m128n64_p3_sk8"),
     };
 }
 

@@ -40,9 +40,13 @@ namespace pt {
 constexpr int kTcTf32 = 0;
 constexpr int kTcBf16x3 = 1;
 
-template <int KIND_, int BN_, int STAGES_>
+template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1>
 struct Tc {
-    static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_;
+    static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_, SPLITK = SPLITK_;
+    // Split-K: SPLITK CTAs of a cluster (1,1,SPLITK) split the k-tiles; their
+    // FP32 partial tiles are summed through distributed shared memory in
+    // cluster-rank order (the pipeline's shared memory is reused for them).
+    static constexpr int RED_LD = BN + 4;
     static constexpr int ELEM = KIND == kTcTf32 ? 4 : 2;  // bytes per plane element
     static constexpr int P = KIND == kTcTf32 ? 2 : 3;     // planes per operand
     static constexpr int BK = 128 / ELEM;                 // one 128-byte swizzle row per tile row
@@ -72,6 +76,11 @@ struct Tc {
     static constexpr uint32_t IDESC =
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
+    static_assert(SPLITK == 1 || BM * RED_LD * 4 <= BAR_OFFSET, "split-K partial tile fits the pipeline memory");
+    static_assert(BM % SPLITK == 0, "split-K reduction slices rows");
+    // Consecutive CTAs walk GROUP_M tile rows down before moving right, so a
+    // wave's A and B panels stay in L2.
+    static constexpr int GROUP_M = 8;
     static_assert(TMEM_COLS <= 512, "tensor memory columns");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
@@ -244,8 +253,27 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         reinterpret_cast<const volatile uint32_t *>(smem_raw + (tslot - raw));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * V::BM, n0 = blockIdx.x * BN;
-    const int nkt = (args.K + BK - 1) / BK;
+    // Grouped rasterisation of the 1-D tile index (blockIdx.x).
+    const int tiles_m = (args.M + V::BM - 1) / V::BM, tiles_n = (args.N + BN - 1) / BN;
+    int m0, n0;
+    {
+        const int t = (int)blockIdx.x;
+        const int per_group = V::GROUP_M * tiles_n;
+        const int first_m = (t / per_group) * V::GROUP_M;
+        const int gsize = tiles_m - first_m < V::GROUP_M ? tiles_m - first_m : V::GROUP_M;
+        const int r = t % per_group;
+        m0 = (first_m + r % gsize) * V::BM;
+        n0 = (r / gsize) * BN;
+    }
+    // K range (k-tiles) of this CTA.
+    const int kt_total = (args.K + BK - 1) / BK;
+    int kt0 = 0, nkt = kt_total;
+    if constexpr (V::SPLITK > 1) {
+        const int per = (kt_total + V::SPLITK - 1) / V::SPLITK;
+        kt0 = (int)blockIdx.z * per;
+        const int kt_end = kt0 + per < kt_total ? kt0 + per : kt_total;
+        nkt = kt_end > kt0 ? kt_end - kt0 : 0;
+    }
     const int nchunks = (nkt + CKT - 1) / CKT;
 
     if (tid == 0) {
@@ -292,11 +320,11 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::STAGE_BYTES);
 #pragma unroll
                 for (int p = 0; p < P; ++p)
-                    tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, kt * BK, m0, p);
+                    tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, (kt0 + kt) * BK, m0, p);
 #pragma unroll
                 for (int p = 0; p < P; ++p)
-                    tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s, kt * BK, n0,
-                                p);
+                    tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s,
+                                (kt0 + kt) * BK, n0, p);
             }
             s_issued = kt;
         }
@@ -367,34 +395,77 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     __syncthreads();
     const bool failed = s_fail != 0;
 
-    if (!failed && warp < V::EPI_WARPS) {
-        const int row = m0 + (warp & 3) * 32 + lane;
-        const int cbase = n0 + (warp >> 2) * COLS;
-        const float alpha = args.alpha, beta = args.beta;
-        if (row < args.M && cbase < args.N) {
-            float *cp = args.C + (int64_t)row * args.ldc + cbase;
-            const int ncol = args.N - cbase;
-            if (ncol >= COLS && args.vec4) {
+    const float alpha = args.alpha, beta = args.beta;
+    if constexpr (V::SPLITK == 1) {
+        if (!failed && warp < V::EPI_WARPS) {
+            const int row = m0 + (warp & 3) * 32 + lane;
+            const int cbase = n0 + (warp >> 2) * COLS;
+            if (row < args.M && cbase < args.N) {
+                float *cp = args.C + (int64_t)row * args.ldc + cbase;
+                const int ncol = args.N - cbase;
+                if (ncol >= COLS && args.vec4) {
 #pragma unroll
-                for (int q = 0; q < COLS; q += 4) {
-                    float4 v = make_float4(alpha * racc[q], alpha * racc[q + 1], alpha * racc[q + 2],
-                                           alpha * racc[q + 3]);
-                    if (beta != 0.f) {
-                        const float4 o = *reinterpret_cast<const float4 *>(cp + q);
-                        v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+                    for (int q = 0; q < COLS; q += 4) {
+                        float4 v = make_float4(alpha * racc[q], alpha * racc[q + 1], alpha * racc[q + 2],
+                                               alpha * racc[q + 3]);
+                        if (beta != 0.f) {
+                            const float4 o = *reinterpret_cast<const float4 *>(cp + q);
+                            v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+                        }
+                        *reinterpret_cast<float4 *>(cp + q) = v;
                     }
-                    *reinterpret_cast<float4 *>(cp + q) = v;
-                }
-            } else {
+                } else {
 #pragma unroll
-                for (int q = 0; q < COLS; ++q) {
-                    if (q < ncol) {
-                        const float v = alpha * racc[q];
-                        cp[q] = (beta != 0.f) ? v + beta * cp[q] : v;
+                    for (int q = 0; q < COLS; ++q) {
+                        if (q < ncol) {
+                            const float v = alpha * racc[q];
+                            cp[q] = (beta != 0.f) ? v + beta * cp[q] : v;
+                        }
                     }
                 }
             }
         }
+    } else {
+        // Every MMA and TMA copy of this CTA has completed (the last chunk was
+        // drained), so the pipeline memory holds the partial tile.
+        float *red = reinterpret_cast<float *>(smem_raw + (sbase - raw));
+        if (warp < V::EPI_WARPS) {
+            float *rrow = red + ((warp & 3) * 32 + lane) * V::RED_LD + (warp >> 2) * COLS;
+#pragma unroll
+            for (int q = 0; q < COLS; q += 4)
+                *reinterpret_cast<float4 *>(rrow + q) = make_float4(racc[q], racc[q + 1], racc[q + 2], racc[q + 3]);
+        }
+        cluster_sync();
+        const uint32_t rank = cluster_ctarank();
+        constexpr int ROWS = V::BM / V::SPLITK, C4 = BN / 4;
+        const uint32_t red_addr = smem_u32(red);
+        for (int idx = tid; idx < ROWS * C4; idx += V::THREADS) {
+            const int rl = (int)rank * ROWS + idx / C4, cl = (idx % C4) * 4;
+            const int row = m0 + rl, col = n0 + cl;
+            if (failed || row >= args.M || col >= args.N) continue;
+            const uint32_t a = red_addr + (uint32_t)(rl * V::RED_LD + cl) * 4u;
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < V::SPLITK; ++q) {
+                const float4 v = ld_dsmem_f4(mapa_shared(a, (uint32_t)q));
+                sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+            }
+            float *cp = args.C + (int64_t)row * args.ldc + col;
+            const float r4[4] = {sum.x, sum.y, sum.z, sum.w};
+            if (args.N - col >= 4 && args.vec4) {
+                float4 o = make_float4(alpha * r4[0], alpha * r4[1], alpha * r4[2], alpha * r4[3]);
+                if (beta != 0.f) {
+                    const float4 c = *reinterpret_cast<const float4 *>(cp);
+                    o.x += beta * c.x; o.y += beta * c.y; o.z += beta * c.z; o.w += beta * c.w;
+                }
+                *reinterpret_cast<float4 *>(cp) = o;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (col + q < args.N) cp[q] = (beta != 0.f) ? alpha * r4[q] + beta * cp[q] : alpha * r4[q];
+            }
+        }
+        cluster_sync();  // no CTA leaves while a peer may still read its tile
     }
     if (tid == 0) {
         // No MMA may still write tensor memory when it is freed, and no TMA
