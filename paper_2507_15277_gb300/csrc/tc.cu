@@ -121,9 +121,21 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     t.beta = a.beta;
     t.vec4 = (!misaligned(a.C, 16) && a.ldc % 4 == 0) ? 1 : 0;
     t.err = a.err;
+    // SPLITK == 1: persistent, one CTA per SM (shared memory allows one).
+    int64_t grid = tiles;
+    if (V::SPLITK == 1) {
+        static std::atomic<int> sm_count[64];
+        int sms = dev < 64 ? sm_count[dev].load(std::memory_order_relaxed) : 0;
+        if (sms <= 0) {
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (sms <= 0) sms = 1;
+            if (dev < 64) sm_count[dev].store(sms, std::memory_order_relaxed);
+        }
+        if (grid > sms) grid = sms;
+    }
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3((unsigned)tiles, 1, V::SPLITK);
+    cfg.gridDim = dim3((unsigned)grid, 1, V::SPLITK);
     cfg.blockDim = dim3(V::THREADS, 1, 1);
     cfg.dynamicSmemBytes = V::SMEM_BYTES;
     cfg.stream = st;

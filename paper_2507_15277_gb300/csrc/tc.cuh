@@ -234,6 +234,22 @@ struct TcArgs {
     int *err;
 };
 
+// Tile coordinates of 1-D tile index t: consecutive indices walk GROUP_M
+// tile rows down before moving right (keeps a wave's panels in L2).
+template <class V>
+__device__ __forceinline__ void tc_tile_coords(int t, int tiles_m, int tiles_n, int &m0, int &n0) {
+    const int per_group = V::GROUP_M * tiles_n;
+    const int first_m = (t / per_group) * V::GROUP_M;
+    const int gsize = tiles_m - first_m < V::GROUP_M ? tiles_m - first_m : V::GROUP_M;
+    const int r = t % per_group;
+    m0 = (first_m + r % gsize) * V::BM;
+    n0 = (r / gsize) * V::BN;
+}
+
+// SPLITK == 1: persistent; CTA b computes tiles b, b + gridDim.x, ...  The
+// stage / phase and chunk / buffer counters run on across tiles, so the
+// producer and the MMA warp start the next tile while the epilogue warps are
+// still storing the previous one.  SPLITK > 1: one tile per cluster of CTAs.
 template <class V>
 __global__ void __launch_bounds__(V::THREADS, 1)
     tc_sgemm_kernel(const TcArgs args, const __grid_constant__ CUtensorMap mapA,
@@ -253,19 +269,11 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         reinterpret_cast<const volatile uint32_t *>(smem_raw + (tslot - raw));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // Grouped rasterisation of the 1-D tile index (blockIdx.x).
     const int tiles_m = (args.M + V::BM - 1) / V::BM, tiles_n = (args.N + BN - 1) / BN;
-    int m0, n0;
-    {
-        const int t = (int)blockIdx.x;
-        const int per_group = V::GROUP_M * tiles_n;
-        const int first_m = (t / per_group) * V::GROUP_M;
-        const int gsize = tiles_m - first_m < V::GROUP_M ? tiles_m - first_m : V::GROUP_M;
-        const int r = t % per_group;
-        m0 = (first_m + r % gsize) * V::BM;
-        n0 = (r / gsize) * BN;
-    }
-    // K range (k-tiles) of this CTA.
+    const int tiles = tiles_m * tiles_n;
+    const int t_first = (int)blockIdx.x;
+    const int t_step = V::SPLITK > 1 ? tiles : (int)gridDim.x;  // split-K: exactly one tile
+    // K range (k-tiles) of this CTA; the same for every tile.
     const int kt_total = (args.K + BK - 1) / BK;
     int kt0 = 0, nkt = kt_total;
     if constexpr (V::SPLITK > 1) {
@@ -302,92 +310,142 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot_ptr;
 
+    const float alpha = args.alpha, beta = args.beta;
     float racc[COLS];
-#pragma unroll
-    for (int j = 0; j < COLS; ++j) racc[j] = 0.f;
     bool epi_ok = true;
 
     if (warp == V::PRODUCER_WARP) {
         if (lane == 0) {
-            int kt = 0;
-            for (; kt < nkt; ++kt) {
-                const int s = kt % STAGES, u = kt / STAGES;
-                if (kt >= STAGES && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)((u - 1) & 1), kWaitLimitNs)) {
-                    s_fail = 1;
-                    break;
+            int g = 0;  // k-tiles issued so far (all tiles)
+            bool ok = true;
+            for (int t = t_first; ok && t < tiles; t += t_step) {
+                int m0, n0;
+                tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const int s = g % STAGES, u = g / STAGES;
+                    if (g >= STAGES && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)((u - 1) & 1), kWaitLimitNs)) {
+                        s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = sbase + s * V::STAGE_BYTES;
+                    mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::STAGE_BYTES);
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, (kt0 + kt) * BK, m0, p);
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s,
+                                    (kt0 + kt) * BK, n0, p);
                 }
-                const uint32_t st = sbase + s * V::STAGE_BYTES;
-                mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::STAGE_BYTES);
-#pragma unroll
-                for (int p = 0; p < P; ++p)
-                    tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, (kt0 + kt) * BK, m0, p);
-#pragma unroll
-                for (int p = 0; p < P; ++p)
-                    tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s,
-                                (kt0 + kt) * BK, n0, p);
             }
-            s_issued = kt;
+            s_issued = g;
         }
     } else if (warp == V::MMA_WARP) {
         if (lane == 0) {
-            int kt = 0;
-            for (; kt < nkt; ++kt) {
-                const int s = kt % STAGES, u = kt / STAGES;
-                const int c = kt / CKT, b = c & 1;
-                const bool first = (kt % CKT) == 0;
-                // Buffer b was last used by chunk c - 2; wait until it is drained.
-                if (first && c >= 2 &&
-                    !mbar_wait_bounded(acce0 + 8 * b, (uint32_t)(((c >> 1) - 1) & 1), kWaitLimitNs)) {
-                    s_fail = 1;
-                    break;
+            int g = 0, c = 0, b = 0;  // k-tiles consumed, chunks started (all tiles)
+            bool ok = true;
+            for (int t = t_first; ok && t < tiles; t += t_step) {
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const int s = g % STAGES, u = g / STAGES;
+                    const bool first = (kt % CKT) == 0;
+                    if (first) {
+                        b = c & 1;
+                        // Buffer b was last used by chunk c - 2; wait until it is drained.
+                        if (c >= 2 && !mbar_wait_bounded(acce0 + 8 * b, (uint32_t)(((c >> 1) - 1) & 1), kWaitLimitNs)) {
+                            s_fail = 1;
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs)) {
+                        s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = sbase + s * V::STAGE_BYTES;
+                    const uint32_t dt = tmem + (uint32_t)(b * BN);
+#pragma unroll
+                    for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
+#pragma unroll
+                        for (int q = 0; q < V::NPROD; ++q) {
+                            int pa, pb;
+                            tc_product<V::KIND>(q, pa, pb);
+                            const uint64_t ad = sw128_kmajor_desc(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                            const uint64_t bd = sw128_kmajor_desc(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
+                                                (uint64_t)(2 * kk);
+                            tc_mma<V::KIND>(dt, ad, bd, V::IDESC, (first && kk == 0 && q == 0) ? 0u : 1u);
+                        }
+                    }
+                    tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
+                    if ((kt % CKT) == CKT - 1 || kt == nkt - 1) {
+                        tc_commit(accf0 + 8 * b);  // chunk c complete
+                        ++c;
+                    }
                 }
-                if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs)) {
-                    s_fail = 1;
+            }
+            tc_commit(doneb);  // every MMA issued so far (also after a failure)
+            s_consumed = g;
+        }
+    } else {
+        // Epilogue warps: drain each chunk's accumulator into FP32 registers,
+        // then store the tile (SPLITK == 1) or keep it for the reduction.
+        const int sub = warp & 3, grp = warp >> 2;
+        const uint32_t lane_base = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(grp * COLS);
+        int c = 0;  // chunks drained (all tiles)
+        for (int t = t_first; epi_ok && t < tiles; t += t_step) {
+#pragma unroll
+            for (int j = 0; j < COLS; ++j) racc[j] = 0.f;
+            for (int ch = 0; ch < nchunks; ++ch, ++c) {
+                const int b = c & 1;
+                const bool ok = mbar_wait_bounded(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), kWaitLimitNs);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    epi_ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t st = sbase + s * V::STAGE_BYTES;
-                const uint32_t dt = tmem + (uint32_t)(b * BN);
 #pragma unroll
-                for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
+                for (int j = 0; j < COLS; j += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(lane_base + (uint32_t)(b * BN + j), r);
 #pragma unroll
-                    for (int q = 0; q < V::NPROD; ++q) {
-                        int pa, pb;
-                        tc_product<V::KIND>(q, pa, pb);
-                        const uint64_t ad = sw128_kmajor_desc(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
-                        const uint64_t bd =
-                            sw128_kmajor_desc(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) + (uint64_t)(2 * kk);
-                        tc_mma<V::KIND>(dt, ad, bd, V::IDESC, (first && kk == 0 && q == 0) ? 0u : 1u);
+                    for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce0 + 8 * b);
+            }
+            if (V::SPLITK == 1 && epi_ok) {
+                int m0, n0;
+                tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
+                const int row = m0 + sub * 32 + lane;
+                const int cbase = n0 + grp * COLS;
+                if (row < args.M && cbase < args.N) {
+                    float *cp = args.C + (int64_t)row * args.ldc + cbase;
+                    const int ncol = args.N - cbase;
+                    if (ncol >= COLS && args.vec4) {
+#pragma unroll
+                        for (int q = 0; q < COLS; q += 4) {
+                            float4 v = make_float4(alpha * racc[q], alpha * racc[q + 1], alpha * racc[q + 2],
+                                                   alpha * racc[q + 3]);
+                            if (beta != 0.f) {
+                                const float4 o = *reinterpret_cast<const float4 *>(cp + q);
+                                v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+                            }
+                            *reinterpret_cast<float4 *>(cp + q) = v;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < COLS; ++q) {
+                            if (q < ncol) {
+                                const float v = alpha * racc[q];
+                                cp[q] = (beta != 0.f) ? v + beta * cp[q] : v;
+                            }
+                        }
                     }
                 }
-                tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
-                if ((kt % CKT) == CKT - 1 || kt == nkt - 1) tc_commit(accf0 + 8 * b);  // chunk c complete
             }
-            tc_commit(doneb);  // every MMA issued so far (also after a failure)
-            s_consumed = kt;
-        }
-    } else {
-        // Epilogue warps: drain each chunk's accumulator into FP32 registers.
-        const int sub = warp & 3, grp = warp >> 2;
-        const uint32_t lane_base = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(grp * COLS);
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = c & 1;
-            const bool ok = mbar_wait_bounded(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), kWaitLimitNs);
-            if (!__all_sync(0xffffffffu, ok)) {
-                epi_ok = false;
-                break;
-            }
-            tc_fence_after();
-#pragma unroll
-            for (int j = 0; j < COLS; j += 32) {
-                uint32_t r[32];
-                tmem_ld32(lane_base + (uint32_t)(b * BN + j), r);
-#pragma unroll
-                for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce0 + 8 * b);
         }
     }
     __syncthreads();
@@ -395,42 +453,20 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     __syncthreads();
     const bool failed = s_fail != 0;
 
-    const float alpha = args.alpha, beta = args.beta;
-    if constexpr (V::SPLITK == 1) {
-        if (!failed && warp < V::EPI_WARPS) {
-            const int row = m0 + (warp & 3) * 32 + lane;
-            const int cbase = n0 + (warp >> 2) * COLS;
-            if (row < args.M && cbase < args.N) {
-                float *cp = args.C + (int64_t)row * args.ldc + cbase;
-                const int ncol = args.N - cbase;
-                if (ncol >= COLS && args.vec4) {
-#pragma unroll
-                    for (int q = 0; q < COLS; q += 4) {
-                        float4 v = make_float4(alpha * racc[q], alpha * racc[q + 1], alpha * racc[q + 2],
-                                               alpha * racc[q + 3]);
-                        if (beta != 0.f) {
-                            const float4 o = *reinterpret_cast<const float4 *>(cp + q);
-                            v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
-                        }
-                        *reinterpret_cast<float4 *>(cp + q) = v;
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < COLS; ++q) {
-                        if (q < ncol) {
-                            const float v = alpha * racc[q];
-                            cp[q] = (beta != 0.f) ? v + beta * cp[q] : v;
-                        }
-                    }
-                }
-            }
-        }
-    } else {
-        // Every MMA and TMA copy of this CTA has completed (the last chunk was
-        // drained), so the pipeline memory holds the partial tile.
+    if constexpr (V::SPLITK > 1) {
+        // One tile per CTA: every MMA and TMA copy of this CTA has completed
+        // (the last chunk was drained), so the pipeline memory can hold the
+        // partial tile; CTA r of the cluster then sums rows
+        // [r*BM/S, (r+1)*BM/S) over ranks 0..S-1 in order.
+        int m0 = 0, n0 = 0;
+        if (t_first < tiles) tc_tile_coords<V>(t_first, tiles_m, tiles_n, m0, n0);
         float *red = reinterpret_cast<float *>(smem_raw + (sbase - raw));
         if (warp < V::EPI_WARPS) {
             float *rrow = red + ((warp & 3) * 32 + lane) * V::RED_LD + (warp >> 2) * COLS;
+            if (nchunks == 0) {
+#pragma unroll
+                for (int j = 0; j < COLS; ++j) racc[j] = 0.f;
+            }
 #pragma unroll
             for (int q = 0; q < COLS; q += 4)
                 *reinterpret_cast<float4 *>(rrow + q) = make_float4(racc[q], racc[q + 1], racc[q + 2], racc[q + 3]);
@@ -442,7 +478,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         for (int idx = tid; idx < ROWS * C4; idx += V::THREADS) {
             const int rl = (int)rank * ROWS + idx / C4, cl = (idx % C4) * 4;
             const int row = m0 + rl, col = n0 + cl;
-            if (failed || row >= args.M || col >= args.N) continue;
+            if (failed || t_first >= tiles || row >= args.M || col >= args.N) continue;
             const uint32_t a = red_addr + (uint32_t)(rl * V::RED_LD + cl) * 4u;
             float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -455,8 +491,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             if (args.N - col >= 4 && args.vec4) {
                 float4 o = make_float4(alpha * r4[0], alpha * r4[1], alpha * r4[2], alpha * r4[3]);
                 if (beta != 0.f) {
-                    const float4 c = *reinterpret_cast<const float4 *>(cp);
-                    o.x += beta * c.x; o.y += beta * c.y; o.z += beta * c.z; o.w += beta * c.w;
+                    const float4 cc = *reinterpret_cast<const float4 *>(cp);
+                    o.x += beta * cc.x; o.y += beta * cc.y; o.z += beta * cc.z; o.w += beta * cc.w;
                 }
                 *reinterpret_cast<float4 *>(cp) = o;
             } else {
