@@ -262,6 +262,19 @@ int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int64_t N, int6
  * device. */
 int pt_device_status(void);
 
+/* Kernel timer (a measurement aid; the paper has no counterpart).  While it
+ * runs on the calling host thread, every pt_sgemm / pt_sgemm_variant call
+ * records a pair of CUDA events on its stream directly around its main GEMM
+ * kernel, so that the time excludes the tensor-core versions' split kernel
+ * and any host work.  Calls made while their stream is being captured record
+ * nothing.  pt_kernel_timer_stop waits for the recorded events, returns the
+ * summed duration in milliseconds and the number of timed launches (either
+ * pointer may be NULL), and ends timing.  Starting an already running timer
+ * discards what it holds.  PT_ECUDA if an event cannot be created, recorded
+ * or read. */
+int pt_kernel_timer_start(void);
+int pt_kernel_timer_stop(double *total_ms, int *launches);
+
 #ifdef __cplusplus
 }
 #endif

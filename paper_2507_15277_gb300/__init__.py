@@ -147,6 +147,19 @@ def device_status() -> int:
     return _l().pt_device_status()
 
 
+def kernel_timer_start() -> None:
+    """Starts timing the main GEMM kernel of every sgemm call on this thread."""
+    _lib.check(_l().pt_kernel_timer_start(), "pt_kernel_timer_start")
+
+
+def kernel_timer_stop():
+    """Waits for the timed launches; returns (total milliseconds, launches)."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int(0)
+    _lib.check(_l().pt_kernel_timer_stop(ctypes.byref(ms), ctypes.byref(n)), "pt_kernel_timer_stop")
+    return ms.value, n.value
+
+
 # ---- portability tuning --------------------------------------------------------------
 def _shapes(shapes):
     arr = (Shape * len(shapes))()

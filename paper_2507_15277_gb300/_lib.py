@@ -93,6 +93,8 @@ SIGNATURES = {
                                            _p, _i64]),
     "pt_device_status": (ctypes.c_int, []),
     "pt_shutdown": (ctypes.c_int, []),
+    "pt_kernel_timer_start": (ctypes.c_int, []),
+    "pt_kernel_timer_stop": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "pt_sgemm_3xtf32_noalloc": (ctypes.c_int, _GEMM_ARGS),
     "pt_grouped_plan": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int]),
     "pt_sgemm_grouped": (ctypes.c_int, [ctypes.POINTER(Problem), _p, ctypes.c_int, _p]),

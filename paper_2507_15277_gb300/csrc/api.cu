@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <vector>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -38,6 +39,47 @@ int set_error(int code, int arg, const char *fmt, ...) {
 void clear_error() {
     g_msg[0] = 0;
     g_arg = 0;
+}
+
+// ---- kernel timer -----------------------------------------------------------------
+// Event pairs of the current host thread; the events are created on first use
+// and kept for the life of the thread (destroying them at thread exit could
+// run after the CUDA runtime has shut down).
+struct KernelTimer {
+    bool on = false, failed = false;
+    int used = 0;
+    std::vector<cudaEvent_t> ev;
+};
+
+KernelTimer &kernel_timer() {
+    static thread_local KernelTimer t;
+    return t;
+}
+
+void kernel_timer_mark(cudaStream_t st, bool begin) {
+    KernelTimer &t = kernel_timer();
+    if (!t.on || t.failed) return;
+    // An unmatched begin (launch refused after it) is overwritten by the next one.
+    if (begin && (t.used & 1)) --t.used;
+    if (!begin && !(t.used & 1)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        if (!begin) --t.used;
+        return;
+    }
+    if (t.used == (int)t.ev.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            t.failed = true;
+            return;
+        }
+        t.ev.push_back(e);
+    }
+    if (cudaEventRecord(t.ev[t.used], st) != cudaSuccess) {
+        t.failed = true;
+        return;
+    }
+    ++t.used;
 }
 
 // ---- driver entry point and device helpers --------------------------------------
@@ -288,6 +330,42 @@ int pt_sgemm_reference(char transA, char transB, int64_t M, int64_t N, int64_t K
     reference_kernel<<<grid, block, 0, st>>>(g);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PT_OK : set_error(PT_ECUDA, 0, "reference kernel: %s", cudaGetErrorString(e));
+}
+
+int pt_kernel_timer_start(void) {
+    clear_error();
+    KernelTimer &t = kernel_timer();
+    t.used = 0;
+    t.failed = false;
+    t.on = true;
+    return PT_OK;
+}
+
+int pt_kernel_timer_stop(double *total_ms, int *launches) {
+    clear_error();
+    KernelTimer &t = kernel_timer();
+    t.on = false;
+    double sum = 0;
+    int n = 0;
+    bool bad = t.failed;
+    for (int i = 0; i + 1 < t.used && !bad; i += 2) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.ev[i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, t.ev[i], t.ev[i + 1]) != cudaSuccess) {
+            bad = true;
+            break;
+        }
+        sum += ms;
+        ++n;
+    }
+    t.used = 0;
+    if (bad) {
+        cudaGetLastError();
+        return set_error(PT_ECUDA, 0, "kernel timer: an event could not be created, recorded or read");
+    }
+    if (total_ms) *total_ms = sum;
+    if (launches) *launches = n;
+    return PT_OK;
 }
 
 int pt_device_status(void) {

@@ -26,6 +26,20 @@ EncodeTiledFn encode_tiled_fn();
 // cudaSetDevice, so it is queried; the call is cheap).
 int current_device();
 
+// Kernel timer (api.cu): records an event on `st` before (begin = true) or
+// after the main GEMM kernel of a call while pt_kernel_timer_start is active
+// on this host thread; otherwise does nothing.
+void kernel_timer_mark(cudaStream_t st, bool begin);
+
+// Launch attribute: programmatic stream serialization (the kernel may be
+// scheduled while the previous kernel of the stream finishes; every kernel
+// launched this way calls pdl_wait before its first global memory access).
+inline void add_pdl_attr(cudaLaunchAttribute *attrs, unsigned &n) {
+    attrs[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+}
+
 inline bool misaligned(const void *p, int bytes) { return (reinterpret_cast<uintptr_t>(p) % bytes) != 0; }
 
 // 2-D fp32 tensor map: inner extent `inner` (contiguous), outer extent
@@ -113,16 +127,21 @@ int launch_simt(const GemmArgs &a, cudaStream_t st, bool dry) {
     cfg.blockDim = dim3(V::THREADS, 1, 1);
     cfg.dynamicSmemBytes = V::SMEM_BYTES;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
+    unsigned nattr = 0;
     if (V::SPLITK > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 1;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = V::SPLITK;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        attr[nattr].id = cudaLaunchAttributeClusterDimension;
+        attr[nattr].val.clusterDim.x = 1;
+        attr[nattr].val.clusterDim.y = 1;
+        attr[nattr].val.clusterDim.z = V::SPLITK;
+        ++nattr;
     }
+    add_pdl_attr(attr, nattr);
+    cfg.attrs = attr;
+    cfg.numAttrs = nattr;
+    kernel_timer_mark(st, true);
     cudaError_t e = cudaLaunchKernelEx(&cfg, simt_sgemm_kernel<V>, a, mA, mB);
+    kernel_timer_mark(st, false);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "launch: %s", cudaGetErrorString(e));
     return PT_OK;
 }

@@ -141,17 +141,20 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
         g_attr_done.fetch_or(bit, std::memory_order_acq_rel);
     }
 
-    // The split kernels overwrite every plane element that the GEMM reads
+    // The split kernel overwrites every plane element that the GEMM reads
     // (rows x K; the pitch padding is outside the tensor maps), so nothing
     // left in the array by an earlier call is used.
     unsigned char *wA = ws;
     unsigned char *wB = ws + 2 * a_plane;
     const int va = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
     const int vb = (reinterpret_cast<uintptr_t>(B) % 16 == 0 && ldb % 4 == 0) ? 1 : 0;
-    tc_split_kernel<kTcTf32><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)((M + 31) / 32)), 256, 0, st>>>(
-        A, lda, ta, (int)M, (int)K, wA, a_plane, pitch, va);
-    tc_split_kernel<kTcTf32><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)((N + 31) / 32)), 256, 0, st>>>(
-        B, ldb, tb ? 0 : 1, (int)N, (int)K, wB, b_plane, pitch, vb);
+    // One launch splits both operands (grid rows: A's blocks, then B's; the
+    // scratch limit keeps (M + N) / 32 far below the 65535 grid limit).
+    const SplitOperand oa{A, lda, ta, (int)M, wA, a_plane, va};
+    const SplitOperand ob{B, ldb, tb ? 0 : 1, (int)N, wB, b_plane, vb};
+    const int ya = (int)((M + 31) / 32), yb = (int)((N + 31) / 32);
+    tc_split_kernel<kTcTf32><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)(ya + yb)), 256, 0, st>>>(
+        oa, ob, (int)K, pitch, ya);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 

@@ -96,6 +96,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start before the previous kernel of its stream has
+// finished; pdl_wait blocks until that kernel has completed and its memory
+// operations are visible (a no-op for a kernel launched without the
+// attribute), so it precedes every global memory access.  pdl_trigger lets
+// the next such kernel of the stream be scheduled once every CTA of this one
+// has called it or exited; it does not release any memory ordering.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }

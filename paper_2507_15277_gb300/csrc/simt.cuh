@@ -227,7 +227,7 @@ __device__ __forceinline__ void store4(float *__restrict__ c, float4 v, int ncol
 // memory free for the next call).
 template <class V>
 __device__ __forceinline__ void simt_body(const GemmArgs &args, const CUtensorMap *tmA, const CUtensorMap *tmB,
-                                          const int m0, const int n0, const int kz) {
+                                          const int m0, const int n0, const int kz, const bool trigger = false) {
     constexpr int BM = V::BM, BN = V::BN, BK = V::BK, TM = V::TM, TN = V::TN, KL = V::KL;
     constexpr int STAGES = V::STAGES, THREADS = V::THREADS, LM = V::LM, LN = V::LN;
     constexpr bool TMA = V::LOADER == kLoaderTma;
@@ -452,6 +452,10 @@ __device__ __forceinline__ void simt_body(const GemmArgs &args, const CUtensorMa
         __syncthreads();
     }
 
+    // Main loop done: the next kernel of the stream may be scheduled (it
+    // still waits for this one to complete before touching memory).
+    if (trigger) pdl_trigger();
+
     if constexpr (V::F2) {
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -536,7 +540,8 @@ template <class V>
 __global__ void __launch_bounds__(V::THREADS, V::MIN_BLOCKS)
     simt_sgemm_kernel(const GemmArgs args, const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB) {
-    simt_body<V>(args, &tmA, &tmB, (int)blockIdx.y * V::BM, (int)blockIdx.x * V::BN, (int)blockIdx.z);
+    pdl_wait();  // launched with programmatic stream serialization
+    simt_body<V>(args, &tmA, &tmB, (int)blockIdx.y * V::BM, (int)blockIdx.x * V::BN, (int)blockIdx.z, true);
 }
 
 }  // namespace pt

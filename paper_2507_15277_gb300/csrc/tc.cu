@@ -51,7 +51,7 @@ int workspace(cudaStream_t st, size_t need, bool dry, void **out) {
 }
 
 int make_map_3d(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int elem, int64_t inner, int64_t rows,
-                int64_t planes, int64_t pitch_bytes, int64_t plane_bytes, int box_inner, int box_rows) {
+                int64_t planes, int64_t pitch_bytes, int64_t plane_bytes, int box_inner, int box_rows, int swz) {
     EncodeTiledFn fn = encode_tiled_fn();
     if (!fn) return set_error(PT_ECUDA, 0, "cuTensorMapEncodeTiled unavailable");
     (void)elem;
@@ -60,7 +60,8 @@ int make_map_3d(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int 
     cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    swz == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(PT_ECUDA, 0, "cuTensorMapEncodeTiled (3-D) failed (%d)", (int)r);
     return PT_OK;
 }
@@ -70,7 +71,7 @@ inline int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 template <class V>
 int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int64_t tiles = (((int64_t)a.M + V::BM - 1) / V::BM) * (((int64_t)a.N + V::BN - 1) / V::BN);
-    if (tiles > 0x7fffffff || ((int64_t)a.M + 31) / 32 > 65535 || ((int64_t)a.N + 31) / 32 > 65535)
+    if (tiles > 0x7fffffff || ((int64_t)a.M + 31) / 32 + ((int64_t)a.N + 31) / 32 > 65535)
         return set_error(PT_EUNSUPPORTED, 3, "shape too large for this variant's grid");
     // Row pitch: a multiple of 8 elements (16-byte aligned rows, whole
     // 8-column groups for the split kernel's vector stores).
@@ -96,19 +97,28 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     unsigned char *wB = wA + V::P * a_plane;
     const int va = (!misaligned(a.A, 16) && a.lda % 4 == 0) ? 1 : 0;
     const int vb = (!misaligned(a.B, 16) && a.ldb % 4 == 0) ? 1 : 0;
-    tc_split_kernel<V::KIND><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)((a.M + 31) / 32)), 256, 0, st>>>(
-        a.A, a.lda, a.ta, a.M, a.K, wA, a_plane, pitch, va);
-    tc_split_kernel<V::KIND><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)((a.N + 31) / 32)), 256, 0, st>>>(
-        a.B, a.ldb, a.tb ? 0 : 1, a.N, a.K, wB, b_plane, pitch, vb);
-    cudaError_t e = cudaGetLastError();
+    const SplitOperand oa{a.A, a.lda, a.ta, a.M, wA, a_plane, va};
+    const SplitOperand ob{a.B, a.ldb, a.tb ? 0 : 1, a.N, wB, b_plane, vb};
+    const int ya = (a.M + 31) / 32, yb = (a.N + 31) / 32;
+    cudaLaunchConfig_t scfg;
+    std::memset(&scfg, 0, sizeof(scfg));
+    scfg.gridDim = dim3((unsigned)((pitch + 63) / 64), (unsigned)(ya + yb), 1);
+    scfg.blockDim = dim3(256, 1, 1);
+    scfg.stream = st;
+    cudaLaunchAttribute sattr[1];
+    unsigned nsattr = 0;
+    add_pdl_attr(sattr, nsattr);
+    scfg.attrs = sattr;
+    scfg.numAttrs = nsattr;
+    cudaError_t e = cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, oa, ob, (int)a.K, pitch, ya);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 
     const CUtensorMapDataType dt =
         V::KIND == kTcTf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap mA, mB;
-    rc = make_map_3d(&mA, wA, dt, V::ELEM, a.K, a.M, V::P, pitch * V::ELEM, a_plane, V::BK, V::BM);
+    rc = make_map_3d(&mA, wA, dt, V::ELEM, a.K, a.M, V::P, pitch * V::ELEM, a_plane, V::BK, V::BM, V::SWZ);
     if (rc != PT_OK) return rc;
-    rc = make_map_3d(&mB, wB, dt, V::ELEM, a.K, a.N, V::P, pitch * V::ELEM, b_plane, V::BK, V::BN);
+    rc = make_map_3d(&mB, wB, dt, V::ELEM, a.K, a.N, V::P, pitch * V::ELEM, b_plane, V::BK, V::BN, V::SWZ);
     if (rc != PT_OK) return rc;
 
     TcArgs t;
@@ -139,16 +149,21 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     cfg.blockDim = dim3(V::THREADS, 1, 1);
     cfg.dynamicSmemBytes = V::SMEM_BYTES;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
+    unsigned nattr = 0;
     if (V::SPLITK > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 1;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = V::SPLITK;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        attr[nattr].id = cudaLaunchAttributeClusterDimension;
+        attr[nattr].val.clusterDim.x = 1;
+        attr[nattr].val.clusterDim.y = 1;
+        attr[nattr].val.clusterDim.z = V::SPLITK;
+        ++nattr;
     }
+    add_pdl_attr(attr, nattr);
+    cfg.attrs = attr;
+    cfg.numAttrs = nattr;
+    kernel_timer_mark(st, true);
     e = cudaLaunchKernelEx(&cfg, tc_sgemm_kernel<V>, t, mA, mB);
+    kernel_timer_mark(st, false);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "tensor-core kernel: %s", cudaGetErrorString(e));
     return PT_OK;
 }
@@ -195,6 +210,15 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcBf16x3, 64, 3, 2>>("tcbf16x3_m128n64_p3_sk2"),
         tc_entry<Tc<kTcBf16x3, 64, 3, 4>>("tcbf16x3_m128n64_p3_sk4"),
         tc_entry<Tc<kTcBf16x3, 64, 3, 8>>("tcbf16x3_m128n64_p3_sk8"),
+        // 64-byte rows: half-size stages, twice the depth.
+        tc_entry<Tc<kTcTf32, 128, 6, 1, 64>>("tc3xtf32_m128n128_p6_sw64"),
+        tc_entry<Tc<kTcTf32, 64, 8, 1, 64>>("tc3xtf32_m128n64_p8_sw64"),
+        tc_entry<Tc<kTcBf16x3, 128, 4, 1, 64>>("tcbf16x3_m128n128_p4_sw64"),
+        tc_entry<Tc<kTcBf16x3, 64, 6, 1, 64>>("tcbf16x3_m128n64_p6_sw64"),
+        tc_entry<Tc<kTcTf32, 128, 6, 2, 64>>("tc3xtf32_m128n128_p6_sw64_sk2"),
+        tc_entry<Tc<kTcTf32, 128, 6, 4, 64>>("tc3xtf32_m128n128_p6_sw64_sk4"),
+        tc_entry<Tc<kTcBf16x3, 128, 4, 2, 64>>("tcbf16x3_m128n128_p4_sw64_sk2"),
+        tc_entry<Tc<kTcBf16x3, 128, 4, 4, 64>>("tcbf16x3_m128n128_p4_sw64_sk4"),
     };
 }
 

@@ -12,20 +12,30 @@
 // |a*b|, so the result is FP32-accurate; these variants join the FP32 SIMT
 // family as further versions of the same operation.
 //
-// Pipeline (one CTA per 128 x BN output tile):
+// Pipeline (a persistent CTA per SM walks the 128 x BN output tiles; split-K
+// versions: one tile per cluster):
 //   a split kernel writes the planes K-major into the library workspace;
 //   producer warp (one lane): TMA loads of every plane's tile (3-D tensor maps
 //                  over [plane][row][k], 128-byte swizzle), full/empty
 //                  mbarriers per stage;
-//   MMA warp (one lane): tcgen05.mma (cta_group::1, M = 128, N = BN, A and B
+//   MMA warp (one lane): tcgen05.mma (cta_group::1, M = 128, A and B
 //                  K-major from shared-memory descriptors) into one of two
 //                  TMEM accumulators; every 128 values of k (a "chunk") the
-//                  accumulator is committed and the other buffer is used;
+//                  accumulator is committed and the other buffer is used.
+//                  The products are paired along N: the B planes of a stage
+//                  are adjacent in shared memory, so planes j and j+1 form one
+//                  2*BN-row operand and A_i x [B_j | B_j+1] is a single
+//                  N = 2*BN MMA whose left half accumulates A_i B_j and right
+//                  half A_i B_j+1.  The remaining products go to the right
+//                  half.  Each A tile is then read fewer times per k step
+//                  (shared-memory bandwidth is the limit at N = BN); the two
+//                  halves are summed in FP32 by the epilogue;
 //   epilogue warps (4 per 128 columns): tcgen05.ld of their 32 TMEM lanes
-//                  (= rows) after each chunk, added into FP32 registers with
-//                  IEEE round-to-nearest ("promotion": the tensor core's own
-//                  accumulation, which is not IEEE round-to-nearest, then
-//                  spans only 128 products), alpha/beta, stores to C.
+//                  (= rows) after each chunk, both halves added into FP32
+//                  registers with IEEE round-to-nearest ("promotion": the
+//                  tensor core's own accumulation, which is not IEEE
+//                  round-to-nearest, then spans only 128 products),
+//                  alpha/beta, stores to C.
 // Every mbarrier wait is bounded; tensor memory is always freed.
 #pragma once
 
@@ -40,28 +50,37 @@ namespace pt {
 constexpr int kTcTf32 = 0;
 constexpr int kTcBf16x3 = 1;
 
-template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1>
+template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128>
 struct Tc {
     static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_, SPLITK = SPLITK_;
+    // Bytes of k per tile row = the TMA / MMA swizzle span (128 or 64).  A
+    // 64-byte row halves the stage, so twice as many stages fit and the
+    // producer refills a smaller part of the pipeline at a time.
+    static constexpr int SWZ = SWZ_;
+    static_assert(SWZ == 128 || SWZ == 64, "swizzle span");
     // Split-K: SPLITK CTAs of a cluster (1,1,SPLITK) split the k-tiles; their
     // FP32 partial tiles are summed through distributed shared memory in
     // cluster-rank order (the pipeline's shared memory is reused for them).
     static constexpr int RED_LD = BN + 4;
     static constexpr int ELEM = KIND == kTcTf32 ? 4 : 2;  // bytes per plane element
     static constexpr int P = KIND == kTcTf32 ? 2 : 3;     // planes per operand
-    static constexpr int BK = 128 / ELEM;                 // one 128-byte swizzle row per tile row
+    static constexpr int BK = SWZ / ELEM;                 // one swizzle row per tile row
     static constexpr int KSTEP = 32 / ELEM;               // K of one MMA instruction (32 bytes)
     static constexpr int NPROD = KIND == kTcTf32 ? 3 : 6;
+    // MMA instructions per k step after pairing along N (see tc_op).
+    static constexpr int NOPS = KIND == kTcTf32 ? 2 : 4;
     // Promotion: the tensor-core accumulator is restarted every CHUNK_KT
     // k-tiles (128 values of k) and added into FP32 registers with IEEE
     // round-to-nearest, so the accumulation error grows with 128, not K.
     static constexpr int CHUNK_KT = 128 / BK;
-    static constexpr int A_PLANE_BYTES = BM * 128;
-    static constexpr int B_PLANE_BYTES = BN * 128;
+    static constexpr int A_PLANE_BYTES = BM * SWZ;
+    static constexpr int B_PLANE_BYTES = BN * SWZ;
     static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES);
     static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
     static constexpr int SMEM_BYTES = BAR_OFFSET + 8 * (2 * STAGES + 5) + 1024;
-    static constexpr int TMEM_COLS = 2 * BN;  // two accumulator buffers
+    // Accumulator buffer: 2*BN columns (left half, right half); two buffers.
+    static constexpr int ACC_COLS = 2 * BN;
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;
     // Epilogue warps: 4 per 128 columns (a warp reads its 32 TMEM lanes), each
     // thread owns one row and COLS columns; then one producer and one MMA warp.
     static constexpr int COL_GROUPS = BN >= 128 ? BN / 128 : 1;
@@ -75,7 +94,9 @@ struct Tc {
     static constexpr uint32_t FMT = KIND == kTcTf32 ? 2u : 1u;
     static constexpr uint32_t IDESC =
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-    static_assert(BN == 64 || BN == 128 || BN == 256, "N of the MMA");
+    static constexpr uint32_t IDESC_W =
+        (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static_assert(BN == 64 || BN == 128, "N of the MMA (2*BN <= 256)");
     static_assert(SPLITK == 1 || BM * RED_LD * 4 <= BAR_OFFSET, "split-K partial tile fits the pipeline memory");
     static_assert(BM % SPLITK == 0, "split-K reduction slices rows");
     // Consecutive CTAs walk GROUP_M tile rows down before moving right, so a
@@ -85,28 +106,41 @@ struct Tc {
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
-// Plane pair (A plane, B plane) of product q, smallest terms first.
+// MMA q of a k step: A plane pa times B plane pb.  wide: N = 2*BN over the
+// adjacent planes pb and pb+1 (left half of the accumulator += A_pa B_pb,
+// right half += A_pa B_pb+1); otherwise N = BN into the right half.  The
+// first MMA is wide, so the zeroing of a chunk's first k step covers both
+// halves.
+//   3xTF32: A0 [B0|B1] (hh, hl), A1 B0 (lh).
+//   BF16x3: A0 [B0|B1], A1 [B0|B1], A0 B2, A2 B0  (the six b_i b_j, i+j <= 2).
 template <int KIND>
-__device__ __forceinline__ void tc_product(int q, int &pa, int &pb) {
+__device__ __forceinline__ void tc_op(int q, int &pa, int &pb, bool &wide) {
     if constexpr (KIND == kTcTf32) {
-        constexpr int a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+        constexpr int a[2] = {0, 1}, b[2] = {0, 0};
         pa = a[q];
         pb = b[q];
+        wide = q == 0;
     } else {
-        constexpr int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+        constexpr int a[4] = {0, 1, 0, 2}, b[4] = {0, 0, 2, 0};
         pa = a[q];
         pb = b[q];
+        wide = q < 2;
     }
 }
 
-// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
-// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this
-// layout), stride byte offset 1024 B between 8-row groups (bits 32-45),
-// descriptor version 1 (bit 46), swizzle mode 2 = 128 B (bits 61-63).  The
-// tile base is 1024-byte aligned, so the base-offset field is 0.
-__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// Shared-memory matrix descriptor of a K-major tile whose rows are one
+// swizzle span (SWZ = 128 or 64 bytes): start address >> 4 (bits 0-13),
+// leading byte offset 16 B (unused for swizzled K-major layouts), stride byte
+// offset 8 rows x SWZ bytes between 8-row groups (bits 32-45), descriptor
+// version 1 (bit 46), layout type at bits 61-63 (2 = 128-byte swizzle,
+// 4 = 64-byte swizzle).  Tile bases are 1024-byte aligned, so the
+// base-offset field is 0.  Successive MMA K steps within a row advance the
+// start address by 32 bytes.
+template <int SWZ>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
+    constexpr uint64_t layout = SWZ == 128 ? 2 : 4;
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)((8 * SWZ) >> 4) << 32) |
+           ((uint64_t)1 << 46) | (layout << 61);
 }
 
 // ---- splitting --------------------------------------------------------------------
@@ -179,16 +213,40 @@ __device__ __forceinline__ void split_store8(unsigned char *ws, int64_t plane_by
 // consecutive columns of one row with 16-byte stores.  The transposed case
 // goes through shared memory so that the global reads run along r.
 // vec4: src and ld allow 16-byte loads along the contiguous direction.
+// One operand of a split: rows x K values, element (r, k) at src[r * ld + k]
+// (trans = 0) or src[k * ld + r] (trans = 1); planes written to ws.
+struct SplitOperand {
+    const float *src;
+    int64_t ld;
+    int trans;
+    int rows;
+    unsigned char *ws;
+    int64_t plane_bytes;
+    int vec4;  // src and ld allow 16-byte loads
+};
+
+// Both operands in one launch: blocks with blockIdx.y < ya split `a`, the
+// others `b`.  A block converts 32 rows x 64 values of k; transposed sources
+// go through shared memory so that both the loads and the 16-byte plane
+// stores are contiguous.
 template <int KIND>
-__global__ void __launch_bounds__(256) tc_split_kernel(const float *__restrict__ src, int64_t ld, int trans,
-                                                       int rows, int K, unsigned char *ws, int64_t plane_bytes,
-                                                       int64_t pitch, int vec4) {
+__global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, const SplitOperand b, int K,
+                                                       int64_t pitch, int ya) {
     __shared__ float tile[64][33];
-    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+    const bool first = (int)blockIdx.y < ya;
+    const SplitOperand &o = first ? a : b;
+    const int by = first ? (int)blockIdx.y : (int)blockIdx.y - ya;
+    const float *__restrict__ src = o.src;
+    const int64_t ld = o.ld;
+    const int rows = o.rows;
+    const int r0 = by * 32, k0 = blockIdx.x * 64;
     const int tid = threadIdx.x;
     const int r = r0 + (tid >> 3), k = k0 + (tid & 7) * 8;
     float x[8];
-    if (trans) {
+    // Launched with programmatic stream serialization: the previous kernel
+    // (e.g. a GEMM still reading the planes) completes first.
+    pdl_wait();
+    if (o.trans) {
         // tile[kk][rr] <- X(r0 + rr, k0 + kk) = src[(k0 + kk) * ld + r0 + rr]
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -196,7 +254,7 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const float *__restrict__
             const int gk = k0 + kk, gr = r0 + rr;
             const float *p = src + (int64_t)gk * ld + gr;
             float v[4];
-            if (gk < K && gr + 3 < rows && vec4) {
+            if (gk < K && gr + 3 < rows && o.vec4) {
                 const float4 q = *reinterpret_cast<const float4 *>(p);
                 v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
             } else {
@@ -212,7 +270,7 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const float *__restrict__
         for (int i = 0; i < 8; ++i) x[i] = tile[kk + i][rr];
     } else {
         const float *p = src + (int64_t)r * ld + k;
-        if (r < rows && k + 7 < K && vec4) {
+        if (r < rows && k + 7 < K && o.vec4) {
             const float4 q0 = *reinterpret_cast<const float4 *>(p);
             const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
             x[0] = q0.x; x[1] = q0.y; x[2] = q0.z; x[3] = q0.w;
@@ -222,7 +280,8 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const float *__restrict__
             for (int i = 0; i < 8; ++i) x[i] = (r < rows && k + i < K) ? p[i] : 0.f;
         }
     }
-    if (r < rows && k < pitch) split_store8<KIND>(ws, plane_bytes, pitch, r, k, x);
+    if (r < rows && k < pitch) split_store8<KIND>(o.ws, o.plane_bytes, pitch, r, k, x);
+    pdl_trigger();
 }
 
 struct TcArgs {
@@ -309,6 +368,9 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot_ptr;
+    // The prologue above touches no global memory; from here on the previous
+    // kernel of the stream (the split) must have completed.
+    pdl_wait();
 
     const float alpha = args.alpha, beta = args.beta;
     float racc[COLS];
@@ -365,17 +427,19 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t st = sbase + s * V::STAGE_BYTES;
-                    const uint32_t dt = tmem + (uint32_t)(b * BN);
+                    const uint32_t dt = tmem + (uint32_t)(b * V::ACC_COLS);
 #pragma unroll
                     for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
 #pragma unroll
-                        for (int q = 0; q < V::NPROD; ++q) {
+                        for (int q = 0; q < V::NOPS; ++q) {
                             int pa, pb;
-                            tc_product<V::KIND>(q, pa, pb);
-                            const uint64_t ad = sw128_kmajor_desc(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
-                            const uint64_t bd = sw128_kmajor_desc(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
+                            bool wide;
+                            tc_op<V::KIND>(q, pa, pb, wide);
+                            const uint64_t ad = kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                            const uint64_t bd = kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
                                                 (uint64_t)(2 * kk);
-                            tc_mma<V::KIND>(dt, ad, bd, V::IDESC, (first && kk == 0 && q == 0) ? 0u : 1u);
+                            tc_mma<V::KIND>(wide ? dt : dt + (uint32_t)BN, ad, bd, wide ? V::IDESC_W : V::IDESC,
+                                            (first && kk == 0 && q == 0) ? 0u : 1u);
                         }
                     }
                     tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
@@ -408,7 +472,10 @@ __global__ void __launch_bounds__(V::THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < COLS; j += 32) {
                     uint32_t r[32];
-                    tmem_ld32(lane_base + (uint32_t)(b * BN + j), r);
+                    tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + j), r);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
+                    tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + BN + j), r);
 #pragma unroll
                     for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
                 }
@@ -450,6 +517,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     }
     __syncthreads();
     if (!epi_ok) s_fail = 1;
+    pdl_trigger();
     __syncthreads();
     const bool failed = s_fail != 0;
 
