@@ -228,8 +228,16 @@ def single(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    # The main GEMM kernel alone (library events around it; excludes the
+    # tensor-core versions' split kernel).
+    pt.kernel_timer_start()
+    for _ in range(args.steps):
+        pt.sgemm(A, B, C, variant=vid)
+    kms, n = pt.kernel_timer_stop()
+    kms /= max(1, n)
     print(json.dumps({"mode": "single", "variant": pt.variant(vid)["name"], "shape": [M, N, K], "ms": ms,
-                      "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12}))
+                      "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12, "kernel_ms": kms,
+                      "kernel_tflops": 2.0 * M * N * K / (kms * 1e-3) / 1e12}))
     return 0
 
 
@@ -299,26 +307,35 @@ def measured_peaks():
         return {}
 
 
+def source_sha256(files):
+    """sha256 over the named kernel sources (csrc/), in the given order."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2507_15277_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in files:
+        with open(os.path.join(src, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def traffic_for(kernel, shape):
-    """DRAM bytes per launch from the committed ncu summary of this kernel and
-    shape (profiles/traffic.json), or None when no capture of the current
-    kernel source exists."""
+    """DRAM bytes per launch of the main GEMM kernel from the committed ncu
+    summary of this kernel and shape (profiles/traffic.json), or None when no
+    capture of the current kernel source exists (each entry names the source
+    files its kernel is built from and their sha256 at capture time)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    import hashlib
-    src = os.path.join(ROOT, "paper_2507_15277_gb300", "csrc")
-    h = hashlib.sha256()
-    for name in ("simt.cuh", "tc.cuh", "ptx.cuh"):
-        with open(os.path.join(src, name), "rb") as f:
-            h.update(f.read())
     for e in rec.get("captures", []):
-        if e.get("kernel") == kernel and tuple(e.get("shape", ())) == tuple(shape) and \
-                e.get("source_sha256") == h.hexdigest():
-            return e.get("dram_bytes")
+        if e.get("kernel") == kernel and tuple(e.get("shape", ())) == tuple(shape):
+            try:
+                if e.get("source_sha256") == source_sha256(e.get("source_files", [])):
+                    return e.get("dram_bytes")
+            except OSError:
+                return None
     return None
 
 

@@ -153,8 +153,8 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     const SplitOperand oa{A, lda, ta, (int)M, wA, a_plane, va};
     const SplitOperand ob{B, ldb, tb ? 0 : 1, (int)N, wB, b_plane, vb};
     const int ya = (int)((M + 31) / 32), yb = (int)((N + 31) / 32);
-    tc_split_kernel<kTcTf32><<<dim3((unsigned)((pitch + 63) / 64), (unsigned)(ya + yb)), 256, 0, st>>>(
-        oa, ob, (int)K, pitch, ya);
+    const dim3 sgrid((unsigned)((pitch + SPLIT_K_PER_BLOCK - 1) / SPLIT_K_PER_BLOCK), (unsigned)(ya + yb));
+    tc_split_kernel<kTcTf32><<<sgrid, 256, 0, st>>>(oa, ob, (int)K, pitch, ya);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 

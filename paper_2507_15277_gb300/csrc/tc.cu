@@ -60,7 +60,10 @@ int make_map_3d(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int 
     cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    swz == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    swz == 32   ? CU_TENSOR_MAP_SWIZZLE_32B
+                    : swz == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(PT_ECUDA, 0, "cuTensorMapEncodeTiled (3-D) failed (%d)", (int)r);
     return PT_OK;
@@ -102,7 +105,7 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int ya = (a.M + 31) / 32, yb = (a.N + 31) / 32;
     cudaLaunchConfig_t scfg;
     std::memset(&scfg, 0, sizeof(scfg));
-    scfg.gridDim = dim3((unsigned)((pitch + 63) / 64), (unsigned)(ya + yb), 1);
+    scfg.gridDim = dim3((unsigned)((pitch + SPLIT_K_PER_BLOCK - 1) / SPLIT_K_PER_BLOCK), (unsigned)(ya + yb), 1);
     scfg.blockDim = dim3(256, 1, 1);
     scfg.stream = st;
     cudaLaunchAttribute sattr[1];
@@ -219,6 +222,9 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcTf32, 128, 6, 4, 64>>("tc3xtf32_m128n128_p6_sw64_sk4"),
         tc_entry<Tc<kTcBf16x3, 128, 4, 2, 64>>("tcbf16x3_m128n128_p4_sw64_sk2"),
         tc_entry<Tc<kTcBf16x3, 128, 4, 4, 64>>("tcbf16x3_m128n128_p4_sw64_sk4"),
+        // 32-byte rows: one MMA k step per stage, eight or twelve stages.
+        tc_entry<Tc<kTcTf32, 128, 12, 1, 32>>("tc3xtf32_m128n128_p12_sw32"),
+        tc_entry<Tc<kTcBf16x3, 128, 8, 1, 32>>("tcbf16x3_m128n128_p8_sw32"),
     };
 }
 

@@ -44,20 +44,18 @@
 
 #include "ptx.cuh"
 #include "simt.cuh"
+#include "split.cuh"
 
 namespace pt {
-
-constexpr int kTcTf32 = 0;
-constexpr int kTcBf16x3 = 1;
 
 template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128>
 struct Tc {
     static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_, SPLITK = SPLITK_;
-    // Bytes of k per tile row = the TMA / MMA swizzle span (128 or 64).  A
-    // 64-byte row halves the stage, so twice as many stages fit and the
+    // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
+    // A narrower row makes the stage smaller, so more stages fit and the
     // producer refills a smaller part of the pipeline at a time.
     static constexpr int SWZ = SWZ_;
-    static_assert(SWZ == 128 || SWZ == 64, "swizzle span");
+    static_assert(SWZ == 128 || SWZ == 64 || SWZ == 32, "swizzle span");
     // Split-K: SPLITK CTAs of a cluster (1,1,SPLITK) split the k-tiles; their
     // FP32 partial tiles are summed through distributed shared memory in
     // cluster-rank order (the pipeline's shared memory is reused for them).
@@ -129,159 +127,18 @@ __device__ __forceinline__ void tc_op(int q, int &pa, int &pb, bool &wide) {
 }
 
 // Shared-memory matrix descriptor of a K-major tile whose rows are one
-// swizzle span (SWZ = 128 or 64 bytes): start address >> 4 (bits 0-13),
+// swizzle span (SWZ = 128, 64 or 32 bytes): start address >> 4 (bits 0-13),
 // leading byte offset 16 B (unused for swizzled K-major layouts), stride byte
 // offset 8 rows x SWZ bytes between 8-row groups (bits 32-45), descriptor
 // version 1 (bit 46), layout type at bits 61-63 (2 = 128-byte swizzle,
-// 4 = 64-byte swizzle).  Tile bases are 1024-byte aligned, so the
+// 4 = 64-byte, 6 = 32-byte swizzle).  Tile bases are 1024-byte aligned, so the
 // base-offset field is 0.  Successive MMA K steps within a row advance the
 // start address by 32 bytes.
 template <int SWZ>
 __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
-    constexpr uint64_t layout = SWZ == 128 ? 2 : 4;
+    constexpr uint64_t layout = SWZ == 128 ? 2 : (SWZ == 64 ? 4 : 6);
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)((8 * SWZ) >> 4) << 32) |
            ((uint64_t)1 << 46) | (layout << 61);
-}
-
-// ---- splitting --------------------------------------------------------------------
-// Round to nearest even on the TF32 grid (10 explicit mantissa bits) by bit
-// manipulation; infinities and NaNs keep their class.
-__device__ __forceinline__ float tf32_rne(float x) {
-    uint32_t u = __float_as_uint(x);
-    if ((u & 0x7f800000u) != 0x7f800000u) u += 0xfffu + ((u >> 13) & 1u);
-    else if (u & 0x007fffffu) u |= 0x00400000u;
-    return __uint_as_float(u & 0xffffe000u);
-}
-
-__device__ __forceinline__ uint16_t bf16_rne_bits(float x) {
-    uint32_t u = __float_as_uint(x);
-    if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);
-    else if (u & 0x007fffffu) u |= 0x00400000u;
-    return (uint16_t)(u >> 16);
-}
-
-__device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
-
-// Planes of 8 consecutive elements x[0..8) of row r starting at column k
-// (k a multiple of 8, k + 8 <= pitch): one 16-byte store per plane for BF16,
-// two per plane for TF32.  Elements at or beyond K are written as zero.
-template <int KIND>
-__device__ __forceinline__ void split_store8(unsigned char *ws, int64_t plane_bytes, int64_t pitch, int r, int k,
-                                             const float (&x)[8]) {
-    const int64_t off = (int64_t)r * pitch + k;
-    if constexpr (KIND == kTcTf32) {
-        float hi[8], lo[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            hi[i] = tf32_rne(x[i]);
-            lo[i] = tf32_rne(x[i] - hi[i]);
-        }
-        float4 *ph = reinterpret_cast<float4 *>(reinterpret_cast<float *>(ws) + off);
-        float4 *pl = reinterpret_cast<float4 *>(reinterpret_cast<float *>(ws + plane_bytes) + off);
-        ph[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
-        ph[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
-        pl[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
-        pl[1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
-    } else {
-        uint32_t b[3][4];
-#pragma unroll
-        for (int i = 0; i < 8; i += 2) {
-            uint16_t q[3][2];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float v = x[i + j];
-                q[0][j] = bf16_rne_bits(v);
-                const float r1 = v - bf16_to_f32(q[0][j]);
-                q[1][j] = bf16_rne_bits(r1);
-                q[2][j] = bf16_rne_bits(r1 - bf16_to_f32(q[1][j]));
-            }
-#pragma unroll
-            for (int pl = 0; pl < 3; ++pl) b[pl][i / 2] = (uint32_t)q[pl][0] | ((uint32_t)q[pl][1] << 16);
-        }
-#pragma unroll
-        for (int pl = 0; pl < 3; ++pl)
-            *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(ws + pl * plane_bytes) + off) =
-                make_uint4(b[pl][0], b[pl][1], b[pl][2], b[pl][3]);
-    }
-}
-
-// Split of a logical rows x K operand X(r, k) into K-major planes with row
-// pitch `pitch` (a multiple of 8 elements, >= round_up(K, 8)); the padding
-// columns [K, pitch) are written as zero.
-// trans == 0: X(r, k) at src[r*ld + k];  trans == 1: X(r, k) at src[k*ld + r].
-// A block of 256 threads covers 32 rows x 64 columns; every thread writes 8
-// consecutive columns of one row with 16-byte stores.  The transposed case
-// goes through shared memory so that the global reads run along r.
-// vec4: src and ld allow 16-byte loads along the contiguous direction.
-// One operand of a split: rows x K values, element (r, k) at src[r * ld + k]
-// (trans = 0) or src[k * ld + r] (trans = 1); planes written to ws.
-struct SplitOperand {
-    const float *src;
-    int64_t ld;
-    int trans;
-    int rows;
-    unsigned char *ws;
-    int64_t plane_bytes;
-    int vec4;  // src and ld allow 16-byte loads
-};
-
-// Both operands in one launch: blocks with blockIdx.y < ya split `a`, the
-// others `b`.  A block converts 32 rows x 64 values of k; transposed sources
-// go through shared memory so that both the loads and the 16-byte plane
-// stores are contiguous.
-template <int KIND>
-__global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, const SplitOperand b, int K,
-                                                       int64_t pitch, int ya) {
-    __shared__ float tile[64][33];
-    const bool first = (int)blockIdx.y < ya;
-    const SplitOperand &o = first ? a : b;
-    const int by = first ? (int)blockIdx.y : (int)blockIdx.y - ya;
-    const float *__restrict__ src = o.src;
-    const int64_t ld = o.ld;
-    const int rows = o.rows;
-    const int r0 = by * 32, k0 = blockIdx.x * 64;
-    const int tid = threadIdx.x;
-    const int r = r0 + (tid >> 3), k = k0 + (tid & 7) * 8;
-    float x[8];
-    // Launched with programmatic stream serialization: the previous kernel
-    // (e.g. a GEMM still reading the planes) completes first.
-    pdl_wait();
-    if (o.trans) {
-        // tile[kk][rr] <- X(r0 + rr, k0 + kk) = src[(k0 + kk) * ld + r0 + rr]
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int kk = (tid >> 3) + 32 * j, rr = (tid & 7) * 4;
-            const int gk = k0 + kk, gr = r0 + rr;
-            const float *p = src + (int64_t)gk * ld + gr;
-            float v[4];
-            if (gk < K && gr + 3 < rows && o.vec4) {
-                const float4 q = *reinterpret_cast<const float4 *>(p);
-                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = (gk < K && gr + i < rows) ? p[i] : 0.f;
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) tile[kk][rr + i] = v[i];
-        }
-        __syncthreads();
-        const int rr = tid >> 3, kk = (tid & 7) * 8;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = tile[kk + i][rr];
-    } else {
-        const float *p = src + (int64_t)r * ld + k;
-        if (r < rows && k + 7 < K && o.vec4) {
-            const float4 q0 = *reinterpret_cast<const float4 *>(p);
-            const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
-            x[0] = q0.x; x[1] = q0.y; x[2] = q0.z; x[3] = q0.w;
-            x[4] = q1.x; x[5] = q1.y; x[6] = q1.z; x[7] = q1.w;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = (r < rows && k + i < K) ? p[i] : 0.f;
-        }
-    }
-    if (r < rows && k < pitch) split_store8<KIND>(o.ws, o.plane_bytes, pitch, r, k, x);
-    pdl_trigger();
 }
 
 struct TcArgs {

@@ -51,8 +51,8 @@ def test_registry_rules():
             assert d["kind"] in (1, 2) and d["bm"] == 128 and d["bn"] in (64, 128)
             assert d["loader"] == 1 and d["trans_mask"] == 15
             assert d["threads"] == 32 * (4 * max(1, d["bn"] // 128) + 2)  # epilogue + producer + MMA warps
-            row = d["bk"] * (4 if d["kind"] == 1 else 2)  # one swizzle row: 128 or 64 bytes
-            assert row == (64 if "_sw64" in d["name"] else 128)
+            row = d["bk"] * (4 if d["kind"] == 1 else 2)  # one swizzle row: 128, 64 or 32 bytes
+            assert row == (64 if "_sw64" in d["name"] else 32 if "_sw32" in d["name"] else 128)
             continue
         simt.append(i)
         assert d["bm"] % d["wm"] == 0 and d["bn"] % d["wn"] == 0
