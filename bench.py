@@ -248,6 +248,42 @@ def dist_env():
     return rank, world, local
 
 
+# ---- replica coordination (host side; the data path has no collective) --------------
+def shared_out_dir(out_dir, rank, world):
+    """The folder for the timing table and manifests, the same on every rank:
+    the given one, else a fresh one that rank 0 creates and broadcasts."""
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
+        return out_dir
+    if world == 1:
+        return tempfile.mkdtemp(prefix="ptbench_")
+    import torch.distributed as dist
+    obj = [tempfile.mkdtemp(prefix="ptbench_") if rank == 0 else None]
+    dist.broadcast_object_list(obj, src=0)
+    return obj[0]
+
+
+def share_manifest(pt, manifest_path, rank, world, make):
+    """Rank 0 runs make() (tuning + selection, which writes manifest_path);
+    after a barrier every rank installs the same manifest."""
+    if rank == 0:
+        make()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    pt.load_manifest(manifest_path)
+
+
+def whole_job(times_ms, world, device=None):
+    """Max of each time over the ranks (the job ends with its slowest rank)."""
+    import torch
+    t = torch.tensor(times_ms, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 # ---- clocks ----------------------------------------------------------------------------
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -425,13 +461,12 @@ def main():
 
     shapes = sweep_shapes()
     train, held = parity_split()
-    out_dir = args.out_dir or tempfile.mkdtemp(prefix="ptbench_")
-    os.makedirs(out_dir, exist_ok=True)
+    out_dir = shared_out_dir(args.out_dir, rank, world)
     table = args.table or os.path.join(out_dir, "table.csv")
     info = {}
 
     # ---- data collection + selection (rank 0; other ranks reuse its manifest) ----
-    if rank == 0:
+    def collect_and_select():
         t0 = time.perf_counter()
         if not args.table:
             pt.tune(shapes, table, reps_min=5, reps_max=args.tune_reps_max, target_ms=args.tune_target_ms)
@@ -478,9 +513,8 @@ def main():
                     "heldout_selector_pct": 100 * pt.score(table, held, mode=pt.PT_SCORE_SELECTOR, manifest=man),
                     "select_s": dt}
         info["selectors"] = comp
-    barrier()
     manifest = os.path.join(out_dir, "kappa_k%d.json" % args.k)
-    pt.load_manifest(manifest)
+    share_manifest(pt, manifest, rank, world, collect_and_select)
 
     # ---- inputs: pinned host copies and resident device buffers ----
     hostA, hostB, hostC, devA, devB, devC = [], [], [], [], [], []
@@ -625,11 +659,7 @@ def main():
     d2h_ms = copies_ms(lambda: [hostC[i].copy_(devC[i], non_blocking=True) for i in range(len(shapes))])
 
     # Whole-job numbers: max time over ranks, units over all ranks.
-    t_local = torch.tensor([elapsed_ms, e2e_ms, eager_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    elapsed_ms, e2e_ms, eager_ms = [float(x) for x in t_local.tolist()]
+    elapsed_ms, e2e_ms, eager_ms = whole_job([elapsed_ms, e2e_ms, eager_ms], world, dev)
     value = world * step_flops * args.steps / (elapsed_ms * 1e-3) / 1e12
     e2e_value = world * step_flops * args.steps / (e2e_ms * 1e-3) / 1e12
 
