@@ -174,6 +174,8 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     t.beta = beta;
     t.vec4 = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
     t.err = nullptr;
+    t.sk_words = nullptr;  // no stream-K in this entry point
+    t.sk_partials = nullptr;
     const dim3 grid((unsigned)(((N + NoAllocCfg::BN - 1) / NoAllocCfg::BN) * ((M + NoAllocCfg::BM - 1) / NoAllocCfg::BM)));
     tc_sgemm_kernel<NoAllocCfg><<<grid, NoAllocCfg::THREADS, NoAllocCfg::SMEM_BYTES, st>>>(t, mA, mB);
     e = cudaGetLastError();

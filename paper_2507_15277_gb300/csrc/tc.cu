@@ -1,5 +1,7 @@
 // Host side of the split-precision tensor-core variants: workspace for the
 // split planes, tensor maps, launches, registry entries.
+#include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -45,6 +47,13 @@ int workspace(cudaStream_t st, size_t need, bool dry, void **out) {
         cudaGetLastError();
         return set_error(PT_ECUDA, 0, "workspace allocation of %zu bytes: %s", bytes, cudaGetErrorString(err));
     }
+    // The stream-K header (epoch, finished-CTA count, flags) starts at zero.
+    err = cudaMemsetAsync(p, 0, kSkHeaderBytes, st);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        return set_error(PT_ECUDA, 0, "workspace initialisation: %s", cudaGetErrorString(err));
+    }
     e = {p, bytes};
     *out = p;
     return PT_OK;
@@ -81,13 +90,34 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int64_t pitch = ((int64_t)a.K + 7) / 8 * 8;
     const int64_t a_plane = align256((int64_t)a.M * pitch * V::ELEM);
     const int64_t b_plane = align256((int64_t)a.N * pitch * V::ELEM);
-    const size_t need = (size_t)V::P * (size_t)(a_plane + b_plane);
+    const int dev = current_device();
+    // Grid: SPLITK == 1 is persistent, one CTA per SM (shared memory allows
+    // one); stream-K needs every CTA to hold at least one chunk.
+    int64_t grid = tiles;
+    if (V::SPLITK == 1) {
+        static std::atomic<int> sm_count[64];
+        int sms = dev < 64 ? sm_count[dev].load(std::memory_order_relaxed) : 0;
+        if (sms <= 0) {
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (sms <= 0) sms = 1;
+            if (dev < 64) sm_count[dev].store(sms, std::memory_order_relaxed);
+        }
+        if (V::STREAMK) {
+            const int64_t nch = (((int64_t)a.K + V::BK - 1) / V::BK + V::CHUNK_KT - 1) / V::CHUNK_KT;
+            grid = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(sms, kSkMaxGrid), tiles * nch));
+        } else if (grid > sms) {
+            grid = sms;
+        }
+    }
+    // Workspace: stream-K header, stream-K partial tiles, then the planes.
+    const int64_t header = align256((int64_t)kSkHeaderBytes);
+    const int64_t partials = V::STREAMK ? align256(grid * V::BM * V::BN * 4) : 0;
+    const size_t need = (size_t)(header + partials) + (size_t)V::P * (size_t)(a_plane + b_plane);
     void *ws = nullptr;
     int rc = workspace(st, need, dry, &ws);
     if (rc != PT_OK || dry) return rc;
 
     static std::atomic<uint64_t> attr_done{0};
-    const int dev = current_device();
     const uint64_t bit = 1ull << (dev & 63);
     if (!(attr_done.load(std::memory_order_acquire) & bit)) {
         cudaError_t e = cudaFuncSetAttribute(tc_sgemm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -96,7 +126,7 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
         attr_done.fetch_or(bit, std::memory_order_acq_rel);
     }
 
-    unsigned char *wA = static_cast<unsigned char *>(ws);
+    unsigned char *wA = static_cast<unsigned char *>(ws) + header + partials;
     unsigned char *wB = wA + V::P * a_plane;
     const int va = (!misaligned(a.A, 16) && a.lda % 4 == 0) ? 1 : 0;
     const int vb = (!misaligned(a.B, 16) && a.ldb % 4 == 0) ? 1 : 0;
@@ -134,18 +164,8 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     t.beta = a.beta;
     t.vec4 = (!misaligned(a.C, 16) && a.ldc % 4 == 0) ? 1 : 0;
     t.err = a.err;
-    // SPLITK == 1: persistent, one CTA per SM (shared memory allows one).
-    int64_t grid = tiles;
-    if (V::SPLITK == 1) {
-        static std::atomic<int> sm_count[64];
-        int sms = dev < 64 ? sm_count[dev].load(std::memory_order_relaxed) : 0;
-        if (sms <= 0) {
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (sms <= 0) sms = 1;
-            if (dev < 64) sm_count[dev].store(sms, std::memory_order_relaxed);
-        }
-        if (grid > sms) grid = sms;
-    }
+    t.sk_words = static_cast<unsigned *>(ws);
+    t.sk_partials = reinterpret_cast<float *>(static_cast<unsigned char *>(ws) + header);
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)grid, 1, V::SPLITK);
@@ -225,6 +245,12 @@ std::vector<VariantEntry> tc_variants() {
         // 32-byte rows: one MMA k step per stage, eight or twelve stages.
         tc_entry<Tc<kTcTf32, 128, 12, 1, 32>>("tc3xtf32_m128n128_p12_sw32"),
         tc_entry<Tc<kTcBf16x3, 128, 8, 1, 32>>("tcbf16x3_m128n128_p8_sw32"),
+        // Stream-K: equal shares of tiles x chunks per SM.
+        tc_entry<Tc<kTcBf16x3, 128, 2, 1, 128, 1>>("tcbf16x3_m128n128_p2_stk"),
+        tc_entry<Tc<kTcBf16x3, 128, 4, 1, 64, 1>>("tcbf16x3_m128n128_p4_sw64_stk"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 1, 128, 1>>("tcbf16x3_m128n64_p3_stk"),
+        tc_entry<Tc<kTcTf32, 128, 3, 1, 128, 1>>("tc3xtf32_m128n128_p3_stk"),
+        tc_entry<Tc<kTcTf32, 64, 4, 1, 128, 1>>("tc3xtf32_m128n64_p4_stk"),
     };
 }
 

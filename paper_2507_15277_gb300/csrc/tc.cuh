@@ -48,9 +48,15 @@
 
 namespace pt {
 
-template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128>
+template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128, int STREAMK_ = 0>
 struct Tc {
     static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_, SPLITK = SPLITK_;
+    // Stream-K (SPLITK == 1 only): the grid's CTAs split tiles x chunks into
+    // equal contiguous ranges, so no SM idles in a last partial wave of
+    // tiles; a tile shared by several CTAs is finished by the CTA that owns
+    // its last chunk, which adds the others' FP32 partial tiles.
+    static constexpr int STREAMK = STREAMK_;
+    static_assert(STREAMK == 0 || SPLITK == 1, "stream-K replaces split-K");
     // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
     // A narrower row makes the stage smaller, so more stages fit and the
     // producer refills a smaller part of the pipeline at a time.
@@ -148,7 +154,55 @@ struct TcArgs {
     float alpha, beta;
     int vec4;  // C and ldc allow 16-byte stores
     int *err;
+    // Stream-K: words[0] = launches completed on this workspace (the epoch),
+    // words[1] = CTAs of this launch that have finished, words[kSkFlags + 4b
+    // + w] = epoch + 1 once epilogue warp w of CTA b has written its rows of
+    // CTA b's partial tile (partials + b * BM * BN, row-major BM x BN).
+    unsigned *sk_words;
+    float *sk_partials;
 };
+
+constexpr int kSkFlags = 32;                  // first flag word
+constexpr int kSkMaxGrid = 2048;              // flag slots (CTAs)
+constexpr size_t kSkHeaderBytes = 4 * (kSkFlags + 4 * kSkMaxGrid);
+
+// Work of one CTA as segments (tile t, chunks [c0, c1) of the tile's k range;
+// a chunk is 128 values of k).  Tile mode: tiles t_first, t_first + t_step,
+// ..., whole.  Stream-K: the chunk range [lo, hi) of the tiles x chunks
+// sequence, visited tile by tile from the last to the first, so that the
+// partial tile a CTA contributes to a later CTA's tile is written first and
+// the tile it finishes (its first) is done last.
+struct TcWork {
+    int nch;
+    int t_first, t_step, tiles;
+    int64_t lo, hi;
+    bool streamk;
+    __device__ int count() const {
+        if (streamk) return hi > lo ? (int)((hi - 1) / nch - lo / nch + 1) : 0;
+        return t_first < tiles ? (tiles - 1 - t_first) / t_step + 1 : 0;
+    }
+    __device__ void seg(int i, int &t, int &c0, int &c1) const {
+        if (streamk) {
+            t = (int)((hi - 1) / nch) - i;
+            const int64_t base = (int64_t)t * nch;
+            c0 = (int)((lo > base ? lo : base) - base);
+            c1 = (int)((hi < base + nch ? hi : base + nch) - base);
+        } else {
+            t = t_first + i * t_step;
+            c0 = 0;
+            c1 = nch;
+        }
+    }
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // Tile coordinates of 1-D tile index t: consecutive indices walk GROUP_M
 // tile rows down before moving right (keeps a wave's panels in L2).
@@ -188,7 +242,6 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     const int tiles_m = (args.M + V::BM - 1) / V::BM, tiles_n = (args.N + BN - 1) / BN;
     const int tiles = tiles_m * tiles_n;
     const int t_first = (int)blockIdx.x;
-    const int t_step = V::SPLITK > 1 ? tiles : (int)gridDim.x;  // split-K: exactly one tile
     // K range (k-tiles) of this CTA; the same for every tile.
     const int kt_total = (args.K + BK - 1) / BK;
     int kt0 = 0, nkt = kt_total;
@@ -199,6 +252,18 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         nkt = kt_end > kt0 ? kt_end - kt0 : 0;
     }
     const int nchunks = (nkt + CKT - 1) / CKT;
+    TcWork work;
+    work.nch = nchunks;
+    work.t_first = t_first;
+    work.t_step = V::SPLITK > 1 ? tiles : (int)gridDim.x;  // split-K: exactly one tile
+    work.tiles = tiles;
+    work.streamk = V::STREAMK != 0;
+    {
+        const int64_t W = (int64_t)tiles * nchunks, G = gridDim.x;
+        work.lo = (int64_t)blockIdx.x * W / G;
+        work.hi = ((int64_t)blockIdx.x + 1) * W / G;
+    }
+    const int nseg = work.count();
 
     if (tid == 0) {
         prefetch_tensormap(&mapA);
@@ -235,12 +300,15 @@ __global__ void __launch_bounds__(V::THREADS, 1)
 
     if (warp == V::PRODUCER_WARP) {
         if (lane == 0) {
-            int g = 0;  // k-tiles issued so far (all tiles)
+            int g = 0;  // k-tiles issued so far (all segments)
             bool ok = true;
-            for (int t = t_first; ok && t < tiles; t += t_step) {
+            for (int i = 0; ok && i < nseg; ++i) {
+                int t, c0, c1;
+                work.seg(i, t, c0, c1);
                 int m0, n0;
                 tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
-                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                const int kt_end = c1 * CKT < nkt ? c1 * CKT : nkt;
+                for (int kt = c0 * CKT; kt < kt_end; ++kt, ++g) {
                     const int s = g % STAGES, u = g / STAGES;
                     if (g >= STAGES && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)((u - 1) & 1), kWaitLimitNs)) {
                         s_fail = 1;
@@ -262,10 +330,13 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         }
     } else if (warp == V::MMA_WARP) {
         if (lane == 0) {
-            int g = 0, c = 0, b = 0;  // k-tiles consumed, chunks started (all tiles)
+            int g = 0, c = 0, b = 0;  // k-tiles consumed, chunks started (all segments)
             bool ok = true;
-            for (int t = t_first; ok && t < tiles; t += t_step) {
-                for (int kt = 0; kt < nkt; ++kt, ++g) {
+            for (int i = 0; ok && i < nseg; ++i) {
+                int t, c0, c1;
+                work.seg(i, t, c0, c1);
+                const int kt_end = c1 * CKT < nkt ? c1 * CKT : nkt;
+                for (int kt = c0 * CKT; kt < kt_end; ++kt, ++g) {
                     const int s = g % STAGES, u = g / STAGES;
                     const bool first = (kt % CKT) == 0;
                     if (first) {
@@ -300,7 +371,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         }
                     }
                     tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
-                    if ((kt % CKT) == CKT - 1 || kt == nkt - 1) {
+                    if ((kt % CKT) == CKT - 1 || kt == kt_end - 1) {
                         tc_commit(accf0 + 8 * b);  // chunk c complete
                         ++c;
                     }
@@ -314,11 +385,15 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         // then store the tile (SPLITK == 1) or keep it for the reduction.
         const int sub = warp & 3, grp = warp >> 2;
         const uint32_t lane_base = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(grp * COLS);
-        int c = 0;  // chunks drained (all tiles)
-        for (int t = t_first; epi_ok && t < tiles; t += t_step) {
+        int c = 0;  // chunks drained (all segments)
+        unsigned epoch1 = 0;  // stream-K: this launch's flag value
+        if constexpr (V::STREAMK != 0) epoch1 = ld_acquire_u32(args.sk_words) + 1u;
+        for (int i = 0; epi_ok && i < nseg; ++i) {
+            int t, c0, c1;
+            work.seg(i, t, c0, c1);
 #pragma unroll
             for (int j = 0; j < COLS; ++j) racc[j] = 0.f;
-            for (int ch = 0; ch < nchunks; ++ch, ++c) {
+            for (int ch = c0; ch < c1; ++ch, ++c) {
                 const int b = c & 1;
                 const bool ok = mbar_wait_bounded(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -339,6 +414,44 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acce0 + 8 * b);
+            }
+            if (V::STREAMK != 0 && epi_ok && c1 < nchunks) {
+                // Contributor: this CTA's partial tile goes to the workspace;
+                // each warp publishes its 32 rows with its own flag.
+                float *prow = args.sk_partials + ((int64_t)blockIdx.x * V::BM + sub * 32 + lane) * BN + grp * COLS;
+#pragma unroll
+                for (int q = 0; q < COLS; q += 4)
+                    *reinterpret_cast<float4 *>(prow + q) = make_float4(racc[q], racc[q + 1], racc[q + 2], racc[q + 3]);
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) st_release_u32(args.sk_words + kSkFlags + 4 * blockIdx.x + warp, epoch1);
+                continue;
+            }
+            if (V::STREAMK != 0 && epi_ok && c0 > 0) {
+                // Finisher: add the partial tiles of the earlier CTAs that
+                // share this tile (nearest first), after their flags are set.
+                const int64_t tile_lo = (int64_t)t * nchunks, W = (int64_t)tiles * nchunks, G = gridDim.x;
+                for (int j = (int)blockIdx.x - 1; j >= 0; --j) {
+                    const int64_t lo_j = (int64_t)j * W / G, hi_j = ((int64_t)j + 1) * W / G;
+                    if (hi_j <= tile_lo) break;
+                    if (lo_j == hi_j) continue;  // an empty range contributes nothing
+                    const unsigned *flag = args.sk_words + kSkFlags + 4 * j + warp;
+                    const uint64_t t0 = globaltimer_ns();
+                    bool ready = false;
+                    while (!(ready = ld_acquire_u32(flag) == epoch1)) {
+                        if (globaltimer_ns() - t0 > kWaitLimitNs) break;
+                    }
+                    if (!__all_sync(0xffffffffu, ready)) {
+                        epi_ok = false;
+                        break;
+                    }
+                    const float *prow = args.sk_partials + ((int64_t)j * V::BM + sub * 32 + lane) * BN + grp * COLS;
+#pragma unroll
+                    for (int q = 0; q < COLS; q += 4) {
+                        const float4 v = *reinterpret_cast<const float4 *>(prow + q);
+                        racc[q] += v.x; racc[q + 1] += v.y; racc[q + 2] += v.z; racc[q + 3] += v.w;
+                    }
+                }
             }
             if (V::SPLITK == 1 && epi_ok) {
                 int m0, n0;
@@ -377,6 +490,19 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     pdl_trigger();
     __syncthreads();
     const bool failed = s_fail != 0;
+    if constexpr (V::STREAMK != 0) {
+        // The last CTA to finish advances the epoch (every CTA has read it
+        // before counting itself) and re-arms the counter.
+        if (tid == 0) {
+            __threadfence();
+            const unsigned old = atomicAdd(args.sk_words + 1, 1u);
+            if (old == gridDim.x - 1) {
+                args.sk_words[1] = 0u;
+                __threadfence();
+                atomicAdd(args.sk_words, 1u);
+            }
+        }
+    }
 
     if constexpr (V::SPLITK > 1) {
         // One tile per CTA: every MMA and TMA copy of this CTA has completed
