@@ -168,30 +168,34 @@ constexpr size_t kSkHeaderBytes = 4 * (kSkFlags + 4 * kSkMaxGrid);
 
 // Work of one CTA as segments (tile t, chunks [c0, c1) of the tile's k range;
 // a chunk is 128 values of k).  Tile mode: tiles t_first, t_first + t_step,
-// ..., whole.  Stream-K: the chunk range [lo, hi) of the tiles x chunks
-// sequence, visited tile by tile from the last to the first, so that the
-// partial tile a CTA contributes to a later CTA's tile is written first and
-// the tile it finishes (its first) is done last.
+// ..., whole.  Stream-K: first ndp whole tiles in the same strided order
+// (all but the last full wave of tiles, which keeps concurrently processed
+// tiles close together in L2), then the chunk range [lo, hi) of the
+// remaining tiles x chunks, which the CTAs share equally, visited tile by
+// tile from the last to the first: the partial tile a CTA contributes to a
+// later CTA's tile is written first and the tile it finishes comes last.
 struct TcWork {
     int nch;
     int t_first, t_step, tiles;
-    int64_t lo, hi;
     bool streamk;
+    int ndp, sk_tile0;  // stream-K: whole tiles per CTA; first tile of the shared part
+    int64_t lo, hi;     // stream-K: chunk range within the shared part
     __device__ int count() const {
-        if (streamk) return hi > lo ? (int)((hi - 1) / nch - lo / nch + 1) : 0;
+        if (streamk) return ndp + (hi > lo ? (int)((hi - 1) / nch - lo / nch + 1) : 0);
         return t_first < tiles ? (tiles - 1 - t_first) / t_step + 1 : 0;
     }
     __device__ void seg(int i, int &t, int &c0, int &c1) const {
-        if (streamk) {
-            t = (int)((hi - 1) / nch) - i;
-            const int64_t base = (int64_t)t * nch;
-            c0 = (int)((lo > base ? lo : base) - base);
-            c1 = (int)((hi < base + nch ? hi : base + nch) - base);
-        } else {
+        if (!streamk || i < ndp) {
             t = t_first + i * t_step;
             c0 = 0;
             c1 = nch;
+            return;
         }
+        const int u_tile = (int)((hi - 1) / nch) - (i - ndp);
+        t = sk_tile0 + u_tile;
+        const int64_t base = (int64_t)u_tile * nch;
+        c0 = (int)((lo > base ? lo : base) - base);
+        c1 = (int)((hi < base + nch ? hi : base + nch) - base);
     }
 };
 
@@ -258,11 +262,15 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     work.t_step = V::SPLITK > 1 ? tiles : (int)gridDim.x;  // split-K: exactly one tile
     work.tiles = tiles;
     work.streamk = V::STREAMK != 0;
-    {
-        const int64_t W = (int64_t)tiles * nchunks, G = gridDim.x;
-        work.lo = (int64_t)blockIdx.x * W / G;
-        work.hi = ((int64_t)blockIdx.x + 1) * W / G;
-    }
+    // Stream-K: whole tiles for all but the last full wave, then the rest
+    // (one to two waves' worth) shared in chunks.
+    const int G = (int)gridDim.x;
+    const int full_waves = tiles / G;
+    work.ndp = full_waves >= 2 ? full_waves - 1 : 0;
+    work.sk_tile0 = work.ndp * G;
+    const int64_t W_sk = (int64_t)(tiles - work.sk_tile0) * nchunks;
+    work.lo = (int64_t)blockIdx.x * W_sk / G;
+    work.hi = ((int64_t)blockIdx.x + 1) * W_sk / G;
     const int nseg = work.count();
 
     if (tid == 0) {
@@ -430,9 +438,9 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             if (V::STREAMK != 0 && epi_ok && c0 > 0) {
                 // Finisher: add the partial tiles of the earlier CTAs that
                 // share this tile (nearest first), after their flags are set.
-                const int64_t tile_lo = (int64_t)t * nchunks, W = (int64_t)tiles * nchunks, G = gridDim.x;
+                const int64_t tile_lo = (int64_t)(t - work.sk_tile0) * nchunks;
                 for (int j = (int)blockIdx.x - 1; j >= 0; --j) {
-                    const int64_t lo_j = (int64_t)j * W / G, hi_j = ((int64_t)j + 1) * W / G;
+                    const int64_t lo_j = (int64_t)j * W_sk / G, hi_j = ((int64_t)j + 1) * W_sk / G;
                     if (hi_j <= tile_lo) break;
                     if (lo_j == hi_j) continue;  // an empty range contributes nothing
                     const unsigned *flag = args.sk_words + kSkFlags + 4 * j + warp;
