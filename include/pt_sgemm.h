@@ -82,6 +82,13 @@ int pt_sgemm_reference(char transA, char transB, int64_t M, int64_t N, int64_t K
 #define PT_LOADER_CPASYNC 0   /* cp.async global->shared staging            */
 #define PT_LOADER_TMA 1       /* cp.async.bulk.tensor (TMA) + mbarrier       */
 
+/* How a variant's CTAs cover the output (pt_variant_desc_t.schedule). */
+#define PT_SCHED_TILE 0        /* one CTA (or split-K cluster) per tile        */
+#define PT_SCHED_PERSISTENT 1  /* one CTA per SM walks the tiles               */
+#define PT_SCHED_STREAMK 2     /* one CTA per SM; whole tiles for all but the
+                                  last full wave, the rest shared in 128-k
+                                  chunks with partial tiles handed over       */
+
 typedef struct pt_variant_desc {
     int id;
     int bm, bn, bk;    /* CTA tile M x N and K-step                          */
@@ -100,6 +107,7 @@ typedef struct pt_variant_desc {
     int kind;          /* 0 = FP32 SIMT, 1 = 3xTF32 tensor core (tcgen05),
                           2 = BF16x3 tensor core (tcgen05, six products)     */
     int fma2;          /* 1: packed fma.rn.f32x2 register-tile updates       */
+    int schedule;      /* PT_SCHED_*                                         */
     char name[96];     /* stable key used in tables and manifests           */
 } pt_variant_desc_t;
 

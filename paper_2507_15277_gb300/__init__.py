@@ -18,14 +18,15 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import (PT_LOADER_CPASYNC, PT_LOADER_TMA, PT_SCORE_BEST_OF_SET,  # noqa: F401
-                   PT_SCORE_SELECTOR, PT_SELECT_AUTO, PT_SELECT_EXACT, PT_SELECT_GREEDY_SWAP,
-                   PT_SELECT_KMEANS, PT_SELECT_TREE, PtError, Shape, TuneOpts, VariantDesc)
+from ._lib import (PT_LOADER_CPASYNC, PT_LOADER_TMA, PT_SCHED_PERSISTENT,  # noqa: F401
+                   PT_SCHED_STREAMK, PT_SCHED_TILE, PT_SCORE_BEST_OF_SET, PT_SCORE_SELECTOR, PT_SELECT_AUTO,
+                   PT_SELECT_EXACT, PT_SELECT_GREEDY_SWAP, PT_SELECT_KMEANS, PT_SELECT_TREE, PtError, Shape,
+                   TuneOpts, VariantDesc)
 
 __all__ = [
     "sgemm", "reference", "num_variants", "variant", "variants", "variant_by_name", "default_variant",
     "tune", "select", "score", "table_shapes", "load_manifest", "selected_variant", "device_status",
-    "grouped_problems", "upload_problems", "sgemm_grouped",
+    "grouped_problems", "upload_problems", "sgemm_grouped", "kernel_timer_start", "kernel_timer_stop",
     "PtError",
 ]
 

@@ -21,6 +21,9 @@ PT_ETIMEOUT = -6
 
 PT_LOADER_CPASYNC = 0
 PT_LOADER_TMA = 1
+PT_SCHED_TILE = 0
+PT_SCHED_PERSISTENT = 1
+PT_SCHED_STREAMK = 2
 
 PT_SELECT_EXACT = 0
 PT_SELECT_GREEDY_SWAP = 1
@@ -38,7 +41,8 @@ _p = ctypes.c_void_p
 class VariantDesc(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in (
         "id", "bm", "bn", "bk", "wm", "wn", "tm", "tn", "kl", "vec", "stages", "splitk", "loader",
-        "a_kmajor", "threads", "smem_bytes", "trans_mask", "kind", "fma2")] + [("name", ctypes.c_char * 96)]
+        "a_kmajor", "threads", "smem_bytes", "trans_mask", "kind", "fma2", "schedule")] + \
+        [("name", ctypes.c_char * 96)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_ if n != "name"}

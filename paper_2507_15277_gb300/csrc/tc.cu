@@ -208,6 +208,7 @@ VariantEntry tc_entry(const char *name) {
     v.desc.smem_bytes = V::SMEM_BYTES;
     v.desc.trans_mask = 15;
     v.desc.kind = V::KIND == kTcTf32 ? 1 : 2;
+    v.desc.schedule = V::STREAMK ? PT_SCHED_STREAMK : (V::SPLITK > 1 ? PT_SCHED_TILE : PT_SCHED_PERSISTENT);
     std::strncpy(v.desc.name, name, sizeof(v.desc.name) - 1);
     v.launch = launch_tc<V>;
     return v;

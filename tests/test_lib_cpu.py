@@ -51,10 +51,14 @@ def test_registry_rules():
             assert d["kind"] in (1, 2) and d["bm"] == 128 and d["bn"] in (64, 128)
             assert d["loader"] == 1 and d["trans_mask"] == 15
             assert d["threads"] == 32 * (4 * max(1, d["bn"] // 128) + 2)  # epilogue + producer + MMA warps
+            want = (pt.PT_SCHED_STREAMK if d["name"].endswith("_stk") else
+                    pt.PT_SCHED_TILE if d["splitk"] > 1 else pt.PT_SCHED_PERSISTENT)
+            assert d["schedule"] == want
             row = d["bk"] * (4 if d["kind"] == 1 else 2)  # one swizzle row: 128, 64 or 32 bytes
             assert row == (64 if "_sw64" in d["name"] else 32 if "_sw32" in d["name"] else 128)
             continue
         simt.append(i)
+        assert d["schedule"] == pt.PT_SCHED_TILE
         assert d["bm"] % d["wm"] == 0 and d["bn"] % d["wn"] == 0
         assert (d["wm"] // d["tm"]) * (d["wn"] // d["tn"]) * d["kl"] == 32
         assert d["threads"] == 32 * (d["bm"] // d["wm"]) * (d["bn"] // d["wn"])
