@@ -55,9 +55,11 @@ def parse():
     p.add_argument("--single", default=None, metavar="M,N,K",
                    help="profiling mode: run one variant (--variant) on one shape, no tuning")
     p.add_argument("--variant", default=None, help="variant name for --single")
-    p.add_argument("--report", default=None, choices=["splitprec", "grouped"],
+    p.add_argument("--report", default=None, choices=["splitprec", "grouped", "stability", "oracle"],
                    help="splitprec: tensor-core split-precision vs FP32 SIMT on the split-precision shapes; "
-                        "grouped: 512 uneven problems, persistent grouped launch vs separate launches")
+                        "grouped: 512 uneven problems, persistent grouped launch vs separate launches; "
+                        "stability: the sweep tuned twice, rank agreement of the two timing tables; "
+                        "oracle: the FP64 CPU oracle timed at 256^3, 1024^3 and 4096^3")
     return p.parse_args()
 
 
@@ -141,8 +143,8 @@ def report_splitprec(args):
     M=N=K in {1024, 4096, 8192}, 8192x8192x256 and 256x8192x8192, inputs of
     random sign with magnitudes 2^U[-10,10] (seed 3): TFLOP/s of the fastest
     variant of each kind (timed by the tuner) and its normalised error
-    against the FP64 oracle on 64 sampled rows; TF32 cuBLAS throughput at
-    8192^3 as the measured TF32 reference."""
+    against the FP64 oracle on 512 sampled rows (all rows when M <= 512);
+    TF32 cuBLAS throughput at 8192^3 as the measured TF32 reference."""
     import numpy as np
     import torch
 
@@ -174,7 +176,7 @@ def report_splitprec(args):
                 best[kind] = (t, r["variant"])
         A = matrix("logu", 3, M, K)
         B = matrix("logu", 4, K, N)
-        sample = np.sort(np.random.default_rng(si).choice(M, min(64, M), replace=False))
+        sample = np.sort(np.random.default_rng(si).choice(M, min(512, M), replace=False))
         ref = og.gemm(A, B, rows=sample)
         Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
         entry = {"shape": [M, N, K]}
@@ -201,8 +203,113 @@ def report_splitprec(args):
     torch.cuda.synchronize()
     tf32 = 10 * 2.0 * 8192 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12
     torch.backends.cuda.matmul.allow_tf32 = False
-    print(json.dumps({"mode": "splitprec", "inputs": "sign * 2^U[-10,10], seed 3; error on 64 sampled rows",
+    print(json.dumps({"mode": "splitprec", "inputs": "sign * 2^U[-10,10], seed 3; error on 512 sampled rows",
                       "tune_s": tune_s, "tf32_cublas_tflops_8192": tf32, "shapes": res}))
+    return 0
+
+
+def _ranks(x):
+    """Ranks 0..n-1 of x (ties get the mean of their ranks)."""
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    order = np.argsort(x, kind="mergesort")
+    r = np.empty(len(x), dtype=np.float64)
+    r[order] = np.arange(len(x), dtype=np.float64)
+    for v in np.unique(x):
+        idx = np.nonzero(x == v)[0]
+        if len(idx) > 1:
+            r[idx] = r[idx].mean()
+    return r
+
+
+def spearman(a, b):
+    """Spearman rank correlation of two equal-length samples."""
+    import numpy as np
+    ra, rb = _ranks(a), _ranks(b)
+    ra -= ra.mean()
+    rb -= rb.mean()
+    den = float(np.sqrt((ra * ra).sum() * (rb * rb).sum()))
+    return float((ra * rb).sum() / den) if den > 0 else 1.0
+
+
+def report_stability(args):
+    """Timing-table stability: the 64-shape sweep is tuned twice; per shape,
+    the Spearman rank correlation of the valid variants' median times between
+    the two passes, whether the per-shape best variant is the same, and the
+    time the second pass's best needs in the first pass relative to the first
+    pass's best (1.0 when the best agrees)."""
+    import csv
+
+    import numpy as np
+
+    import paper_2507_15277_gb300 as pt
+    from workloads import sweep_shapes
+    shapes = sweep_shapes()
+    out_dir = args.out_dir or tempfile.mkdtemp(prefix="ptstab_")
+    os.makedirs(out_dir, exist_ok=True)
+    paths = [os.path.join(out_dir, "pass%d.csv" % i) for i in (1, 2)]
+    for path in paths:
+        pt.tune(shapes, path, reps_min=5, reps_max=args.tune_reps_max, target_ms=args.tune_target_ms)
+    tabs = []
+    for path in paths:
+        t = {}
+        for r in csv.DictReader(open(path)):
+            if int(r["valid"]):
+                t[(int(r["M"]), int(r["N"]), int(r["K"]), r["variant"])] = float(r["median_ms"])
+        tabs.append(t)
+    per = []
+    for (M, N, K) in shapes:
+        names = sorted({v for (m, n, k, v) in tabs[0] if (m, n, k) == (M, N, K)} &
+                       {v for (m, n, k, v) in tabs[1] if (m, n, k) == (M, N, K)})
+        a = [tabs[0][(M, N, K, v)] for v in names]
+        b = [tabs[1][(M, N, K, v)] for v in names]
+        best1, best2 = names[int(np.argmin(a))], names[int(np.argmin(b))]
+        per.append({"shape": [M, N, K], "variants": len(names), "spearman": spearman(a, b),
+                    "same_best": best1 == best2, "pass1_time_of_pass2_best_rel": tabs[0][(M, N, K, best2)] / min(a)})
+    rho = [p["spearman"] for p in per]
+    print(json.dumps({"mode": "stability", "shapes": len(per),
+                      "spearman_median": float(np.median(rho)), "spearman_min": float(np.min(rho)),
+                      "same_best_fraction": sum(p["same_best"] for p in per) / len(per),
+                      "geomean_pass1_time_of_pass2_best_rel":
+                          float(np.exp(np.mean(np.log([p["pass1_time_of_pass2_best_rel"] for p in per])))),
+                      "per_shape": per}))
+    return 0
+
+
+def report_oracle(args):
+    """The FP64 CPU oracle timed at 256^3, 1024^3 and 4096^3, on one thread and
+    on all of the host's threads (GFLOP/s), with the host CPU model."""
+    import numpy as np
+
+    from oracle import gemm as og
+    from workloads import matrix
+    model = ""
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    nmax = og.num_threads()
+    res = []
+    for n in (256, 1024, 4096):
+        A = matrix("uniform", 1, n, n)
+        B = matrix("uniform", 2, n, n)
+        for threads in (1, nmax):
+            og.set_threads(threads)
+            rows = None
+            if threads == 1 and n == 4096:
+                rows = np.arange(256)  # bounded: 256 of the 4096 rows on one thread
+            og.gemm(A[:8], B, M=8, N=n, K=n)  # warm
+            t0 = time.perf_counter()
+            og.gemm(A, B, M=n, N=n, K=n, rows=rows)
+            dt = time.perf_counter() - t0
+            m = n if rows is None else len(rows)
+            res.append({"shape": [n, n, n], "threads": threads, "rows": m, "s": dt,
+                        "gflops": 2.0 * m * n * n / dt / 1e9})
+    og.set_threads(nmax)
+    print(json.dumps({"mode": "oracle", "cpu": model, "threads_max": nmax, "runs": res}))
     return 0
 
 
@@ -438,6 +545,10 @@ def main():
         return report_splitprec(args)
     if args.report == "grouped":
         return report_grouped(args)
+    if args.report == "stability":
+        return report_stability(args)
+    if args.report == "oracle":
+        return report_oracle(args)
 
     import numpy as np
     import torch
@@ -776,6 +887,7 @@ def main():
         "selectors": info.get("selectors"),
         "tuning": {"tune_s": info.get("tune_s"), "select_s": info.get("select_s"), "table": table},
         "per_shape": [{"shape": list(s), "ms": round(ms, 5), "tflops": round(f / (ms * 1e-3) / 1e12, 3),
+                       "gbs": round(4.0 * (s[0] * s[2] + s[2] * s[1] + s[0] * s[1]) / (ms * 1e-3) / 1e9, 1),
                        "variant": pt.variant(p)["name"], "cublas_tflops": round(f / (cm * 1e-3) / 1e12, 3)}
                       for s, ms, f, p, cm in zip(shapes, shape_ms, flops, picks, cub_ms)],
         "context": {"cublas_sgemm_tflops": cublas_tflops, "cublas_math": "FP32 (allow_tf32=False, precision highest)",
