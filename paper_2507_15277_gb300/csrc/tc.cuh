@@ -81,7 +81,10 @@ struct Tc {
     static constexpr int B_PLANE_BYTES = BN * SWZ;
     static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES);
     static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
-    static constexpr int SMEM_BYTES = BAR_OFFSET + 8 * (2 * STAGES + 5) + 1024;
+    // Barriers (full, empty per stage; two accumulator-full, two
+    // accumulator-empty, MMA-done) and the TMEM address slot.
+    static constexpr int BAR_BYTES = 8 * (2 * STAGES + 6);
+
     // Accumulator buffer: 2*BN columns (left half, right half); two buffers.
     static constexpr int ACC_COLS = 2 * BN;
     static constexpr int TMEM_COLS = 2 * ACC_COLS;
@@ -92,6 +95,15 @@ struct Tc {
     static constexpr int EPI_WARPS = 4 * COL_GROUPS;
     static constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
     static constexpr int THREADS = 32 * (EPI_WARPS + 2);
+    // Epilogue staging (when it fits): each epilogue warp transposes its 32
+    // rows through a 32 x STG_LD float buffer, 32 columns at a time, so that
+    // C is written in whole 128-byte row segments.
+    static constexpr int STG_LD = 36;
+    static constexpr int STG_WARP_FLOATS = 32 * STG_LD;
+    static constexpr int STG_OFFSET = (BAR_OFFSET + BAR_BYTES + 15) / 16 * 16;
+    static constexpr int STG_END = STG_OFFSET + EPI_WARPS * STG_WARP_FLOATS * 4;
+    static constexpr bool STAGE_C = STG_END + 1024 <= 232448;
+    static constexpr int SMEM_BYTES = (STAGE_C ? STG_END : BAR_OFFSET + BAR_BYTES) + 1024;
     // Instruction descriptor: D = F32 (bits 4-5 = 1), A/B format (bits 7-9,
     // 10-12: TF32 = 2, BF16 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
     // bit 17, M >> 4 at bit 24.
@@ -426,10 +438,12 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             if (V::STREAMK != 0 && epi_ok && c1 < nchunks) {
                 // Contributor: this CTA's partial tile goes to the workspace;
                 // each warp publishes its 32 rows with its own flag.
-                float *prow = args.sk_partials + ((int64_t)blockIdx.x * V::BM + sub * 32 + lane) * BN + grp * COLS;
+                // Lane-major layout: a warp writes 512 contiguous bytes per store.
+                float4 *pw = reinterpret_cast<float4 *>(args.sk_partials) +
+                             ((int64_t)blockIdx.x * V::EPI_WARPS + warp) * (COLS / 4) * 32 + lane;
 #pragma unroll
                 for (int q = 0; q < COLS; q += 4)
-                    *reinterpret_cast<float4 *>(prow + q) = make_float4(racc[q], racc[q + 1], racc[q + 2], racc[q + 3]);
+                    pw[(q / 4) * 32] = make_float4(racc[q], racc[q + 1], racc[q + 2], racc[q + 3]);
                 __threadfence();
                 __syncwarp();
                 if (lane == 0) st_release_u32(args.sk_words + kSkFlags + 4 * blockIdx.x + warp, epoch1);
@@ -453,15 +467,57 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         epi_ok = false;
                         break;
                     }
-                    const float *prow = args.sk_partials + ((int64_t)j * V::BM + sub * 32 + lane) * BN + grp * COLS;
+                    const float4 *pr = reinterpret_cast<const float4 *>(args.sk_partials) +
+                                       ((int64_t)j * V::EPI_WARPS + warp) * (COLS / 4) * 32 + lane;
 #pragma unroll
                     for (int q = 0; q < COLS; q += 4) {
-                        const float4 v = *reinterpret_cast<const float4 *>(prow + q);
+                        const float4 v = pr[(q / 4) * 32];
                         racc[q] += v.x; racc[q + 1] += v.y; racc[q + 2] += v.z; racc[q + 3] += v.w;
                     }
                 }
             }
-            if (V::SPLITK == 1 && epi_ok) {
+            if (V::SPLITK == 1 && epi_ok && V::STAGE_C) {
+                // Coalesced store: the warp's 32 x 32 blocks go through its
+                // staging buffer (row = lane in, four rows of 32 columns per
+                // instruction out).
+                int m0, n0;
+                tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
+                float *stg = reinterpret_cast<float *>(smem_raw + (sbase - raw) + V::STG_OFFSET) +
+                             warp * V::STG_WARP_FLOATS;
+                const int rr = lane >> 3, cc = (lane & 7) * 4;
+#pragma unroll
+                for (int jb = 0; jb < COLS; jb += 32) {
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4)
+                        *reinterpret_cast<float4 *>(stg + lane * V::STG_LD + q) =
+                            make_float4(alpha * racc[jb + q], alpha * racc[jb + q + 1], alpha * racc[jb + q + 2],
+                                        alpha * racc[jb + q + 3]);
+                    __syncwarp();
+                    const int col = n0 + grp * COLS + jb + cc;
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int r = it * 4 + rr;
+                        const int row = m0 + sub * 32 + r;
+                        float4 v = *reinterpret_cast<const float4 *>(stg + r * V::STG_LD + cc);
+                        if (row < args.M && col < args.N) {
+                            float *cp = args.C + (int64_t)row * args.ldc + col;
+                            if (args.N - col >= 4 && args.vec4) {
+                                if (beta != 0.f) {
+                                    const float4 o = *reinterpret_cast<const float4 *>(cp);
+                                    v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+                                }
+                                *reinterpret_cast<float4 *>(cp) = v;
+                            } else {
+                                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    if (col + e < args.N) cp[e] = (beta != 0.f) ? vv[e] + beta * cp[e] : vv[e];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            } else if (V::SPLITK == 1 && epi_ok) {
                 int m0, n0;
                 tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
                 const int row = m0 + sub * 32 + lane;
