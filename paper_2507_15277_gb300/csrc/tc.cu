@@ -252,6 +252,14 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcBf16x3, 64, 3, 1, 128, 1>>("tcbf16x3_m128n64_p3_stk"),
         tc_entry<Tc<kTcTf32, 128, 3, 1, 128, 1>>("tc3xtf32_m128n128_p3_stk"),
         tc_entry<Tc<kTcTf32, 64, 4, 1, 128, 1>>("tc3xtf32_m128n64_p4_stk"),
+        // BF16x3 64-column tiles with room for the coalescing epilogue stage.
+        tc_entry<Tc<kTcBf16x3, 64, 2>>("tcbf16x3_m128n64_p2"),
+        tc_entry<Tc<kTcBf16x3, 64, 2, 4>>("tcbf16x3_m128n64_p2_sk4"),
+        tc_entry<Tc<kTcBf16x3, 64, 4, 1, 64>>("tcbf16x3_m128n64_p4_sw64"),
+        tc_entry<Tc<kTcBf16x3, 64, 4, 2, 64>>("tcbf16x3_m128n64_p4_sw64_sk2"),
+        tc_entry<Tc<kTcBf16x3, 64, 4, 4, 64>>("tcbf16x3_m128n64_p4_sw64_sk4"),
+        tc_entry<Tc<kTcBf16x3, 64, 4, 8, 64>>("tcbf16x3_m128n64_p4_sw64_sk8"),
+        tc_entry<Tc<kTcBf16x3, 64, 4, 1, 64, 1>>("tcbf16x3_m128n64_p4_sw64_stk"),
     };
 }
 
