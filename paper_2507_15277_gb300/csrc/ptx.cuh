@@ -96,6 +96,12 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Orders this thread's generic-proxy shared-memory writes before later
+// async-proxy accesses (TMA, tensor-core operand reads) of the same data.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Programmatic dependent launch.  A kernel launched with programmatic stream
 // serialization may start before the previous kernel of its stream has
 // finished; pdl_wait blocks until that kernel has completed and its memory

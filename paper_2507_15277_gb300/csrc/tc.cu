@@ -87,9 +87,11 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
         return set_error(PT_EUNSUPPORTED, 3, "shape too large for this variant's grid");
     // Row pitch: a multiple of 8 elements (16-byte aligned rows, whole
     // 8-column groups for the split kernel's vector stores).
+    if (V::FUSEB && (a.tb || misaligned(a.B, 16) || a.ldb % 4 != 0))
+        return set_error(PT_EUNSUPPORTED, 0, "fused-B variant needs B as K x N (transB = N), 16-byte aligned, ldb %% 4 == 0");
     const int64_t pitch = ((int64_t)a.K + 7) / 8 * 8;
     const int64_t a_plane = align256((int64_t)a.M * pitch * V::ELEM);
-    const int64_t b_plane = align256((int64_t)a.N * pitch * V::ELEM);
+    const int64_t b_plane = V::FUSEB ? 0 : align256((int64_t)a.N * pitch * V::ELEM);
     const int dev = current_device();
     // Grid: SPLITK == 1 is persistent, one CTA per SM (shared memory allows
     // one); stream-K needs every CTA to hold at least one chunk.
@@ -132,7 +134,7 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int vb = (!misaligned(a.B, 16) && a.ldb % 4 == 0) ? 1 : 0;
     const SplitOperand oa{a.A, a.lda, a.ta, a.M, wA, a_plane, va};
     const SplitOperand ob{a.B, a.ldb, a.tb ? 0 : 1, a.N, wB, b_plane, vb};
-    const int ya = (a.M + 31) / 32, yb = (a.N + 31) / 32;
+    const int ya = (a.M + 31) / 32, yb = V::FUSEB ? 0 : (a.N + 31) / 32;
     cudaLaunchConfig_t scfg;
     std::memset(&scfg, 0, sizeof(scfg));
     scfg.gridDim = dim3((unsigned)((pitch + SPLIT_K_PER_BLOCK - 1) / SPLIT_K_PER_BLOCK), (unsigned)(ya + yb), 1);
@@ -151,7 +153,10 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     CUtensorMap mA, mB;
     rc = make_map_3d(&mA, wA, dt, V::ELEM, a.K, a.M, V::P, pitch * V::ELEM, a_plane, V::BK, V::BM, V::SWZ);
     if (rc != PT_OK) return rc;
-    rc = make_map_3d(&mB, wB, dt, V::ELEM, a.K, a.N, V::P, pitch * V::ELEM, b_plane, V::BK, V::BN, V::SWZ);
+    if (V::FUSEB)
+        rc = make_map_2d(&mB, a.B, a.N, a.K, a.ldb, V::BN, V::BK, CU_TENSOR_MAP_SWIZZLE_NONE);
+    else
+        rc = make_map_3d(&mB, wB, dt, V::ELEM, a.K, a.N, V::P, pitch * V::ELEM, b_plane, V::BK, V::BN, V::SWZ);
     if (rc != PT_OK) return rc;
 
     TcArgs t;
@@ -206,7 +211,7 @@ VariantEntry tc_entry(const char *name) {
     v.desc.a_kmajor = 1;
     v.desc.threads = V::THREADS;
     v.desc.smem_bytes = V::SMEM_BYTES;
-    v.desc.trans_mask = 15;
+    v.desc.trans_mask = V::FUSEB ? 5 : 15;  // fused B: transB = 'N' only
     v.desc.kind = V::KIND == kTcTf32 ? 1 : 2;
     v.desc.schedule = V::STREAMK ? PT_SCHED_STREAMK : (V::SPLITK > 1 ? PT_SCHED_TILE : PT_SCHED_PERSISTENT);
     std::strncpy(v.desc.name, name, sizeof(v.desc.name) - 1);
@@ -252,6 +257,11 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcBf16x3, 64, 3, 1, 128, 1>>("tcbf16x3_m128n64_p3_stk"),
         tc_entry<Tc<kTcTf32, 128, 3, 1, 128, 1>>("tc3xtf32_m128n128_p3_stk"),
         tc_entry<Tc<kTcTf32, 64, 4, 1, 128, 1>>("tc3xtf32_m128n64_p4_stk"),
+        // Fused B split (B converted inside the GEMM kernel; small M).
+        tc_entry<Tc<kTcBf16x3, 64, 2, 1, 128, 0, 1>>("tcbf16x3_m128n64_p2_fb"),
+        tc_entry<Tc<kTcBf16x3, 64, 2, 2, 128, 0, 1>>("tcbf16x3_m128n64_p2_fb_sk2"),
+        tc_entry<Tc<kTcBf16x3, 64, 2, 4, 128, 0, 1>>("tcbf16x3_m128n64_p2_fb_sk4"),
+        tc_entry<Tc<kTcBf16x3, 64, 2, 1, 128, 1, 1>>("tcbf16x3_m128n64_p2_fb_stk"),
         // BF16x3 64-column tiles with room for the coalescing epilogue stage.
         tc_entry<Tc<kTcBf16x3, 64, 2>>("tcbf16x3_m128n64_p2"),
         tc_entry<Tc<kTcBf16x3, 64, 2, 4>>("tcbf16x3_m128n64_p2_sk4"),

@@ -48,7 +48,7 @@
 
 namespace pt {
 
-template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128, int STREAMK_ = 0>
+template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128, int STREAMK_ = 0, int FUSEB_ = 0>
 struct Tc {
     static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_, SPLITK = SPLITK_;
     // Stream-K (SPLITK == 1 only): the grid's CTAs split tiles x chunks into
@@ -57,6 +57,12 @@ struct Tc {
     // its last chunk, which adds the others' FP32 partial tiles.
     static constexpr int STREAMK = STREAMK_;
     static_assert(STREAMK == 0 || SPLITK == 1, "stream-K replaces split-K");
+    // Fused B split (BF16x3, B stored K x N with N contiguous): the producer
+    // loads FP32 tiles of B itself and four converter warps write its three
+    // planes into the stage, so B never passes through the split kernel.
+    // Pays where B dominates the traffic (small M).
+    static constexpr int FUSEB = FUSEB_;
+    static_assert(FUSEB == 0 || KIND_ == 1, "fused B split is BF16x3 only");
     // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
     // A narrower row makes the stage smaller, so more stages fit and the
     // producer refills a smaller part of the pipeline at a time.
@@ -79,11 +85,14 @@ struct Tc {
     static constexpr int CHUNK_KT = 128 / BK;
     static constexpr int A_PLANE_BYTES = BM * SWZ;
     static constexpr int B_PLANE_BYTES = BN * SWZ;
-    static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES);
+    static constexpr int BF32_BYTES = FUSEB ? BK * BN * 4 : 0;  // FP32 B tile [BK][BN]
+    static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES) + BF32_BYTES;
+    static constexpr int LOAD_BYTES = FUSEB ? P * A_PLANE_BYTES + BF32_BYTES : STAGE_BYTES;  // TMA bytes
     static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
-    // Barriers (full, empty per stage; two accumulator-full, two
-    // accumulator-empty, MMA-done) and the TMEM address slot.
-    static constexpr int BAR_BYTES = 8 * (2 * STAGES + 6);
+    // Barriers (full, empty per stage; converted per stage when FUSEB; two
+    // accumulator-full, two accumulator-empty, MMA-done) and the TMEM address
+    // slot.
+    static constexpr int BAR_BYTES = 8 * ((FUSEB ? 3 : 2) * STAGES + 6);
 
     // Accumulator buffer: 2*BN columns (left half, right half); two buffers.
     static constexpr int ACC_COLS = 2 * BN;
@@ -94,7 +103,8 @@ struct Tc {
     static constexpr int COLS = BN / COL_GROUPS;
     static constexpr int EPI_WARPS = 4 * COL_GROUPS;
     static constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
-    static constexpr int THREADS = 32 * (EPI_WARPS + 2);
+    static constexpr int CONV_WARP0 = EPI_WARPS + 2, CONV_WARPS = FUSEB ? 4 : 0;
+    static constexpr int THREADS = 32 * (EPI_WARPS + 2 + CONV_WARPS);
     // Epilogue staging (when it fits): each epilogue warp transposes its 32
     // rows through a 32 x STG_LD float buffer, 32 columns at a time, so that
     // C is written in whole 128-byte row segments.
@@ -247,7 +257,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     const uint32_t sbase = (raw + 1023u) & ~1023u;
     const uint32_t full0 = sbase + V::BAR_OFFSET;  // STAGES: TMA landed
     const uint32_t empty0 = full0 + 8 * STAGES;    // STAGES: MMAs done reading
-    const uint32_t accf0 = empty0 + 8 * STAGES;    // 2: accumulator buffer ready
+    const uint32_t conv0 = empty0 + 8 * STAGES;    // STAGES (FUSEB): B planes written
+    const uint32_t accf0 = conv0 + (V::FUSEB ? 8 * STAGES : 0);  // 2: accumulator buffer ready
     const uint32_t acce0 = accf0 + 16;             // 2: accumulator buffer drained
     const uint32_t doneb = acce0 + 16;             // every issued MMA finished
     const uint32_t tslot = doneb + 8;
@@ -291,6 +302,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
+            if (V::FUSEB) mbar_init(conv0 + 8 * s, V::CONV_WARPS);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf0 + 8 * b, 1);
@@ -336,14 +348,20 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         break;
                     }
                     const uint32_t st = sbase + s * V::STAGE_BYTES;
-                    mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::STAGE_BYTES);
+                    mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::LOAD_BYTES);
 #pragma unroll
                     for (int p = 0; p < P; ++p)
                         tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, (kt0 + kt) * BK, m0, p);
+                    if constexpr (V::FUSEB) {
+                        // FP32 tile of B: BK rows of k, BN columns of n (2-D map over B itself).
+                        tma_load_2d(st + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES), &mapB, full0 + 8 * s, n0,
+                                    (kt0 + kt) * BK);
+                    } else {
 #pragma unroll
-                    for (int p = 0; p < P; ++p)
-                        tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s,
-                                    (kt0 + kt) * BK, n0, p);
+                        for (int p = 0; p < P; ++p)
+                            tma_load_3d(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, full0 + 8 * s,
+                                        (kt0 + kt) * BK, n0, p);
+                    }
                 }
             }
             s_issued = g;
@@ -368,7 +386,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                             break;
                         }
                     }
-                    if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs)) {
+                    if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs) ||
+                        (V::FUSEB && !mbar_wait_bounded(conv0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs))) {
                         s_fail = 1;
                         ok = false;
                         break;
@@ -399,6 +418,63 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             }
             tc_commit(doneb);  // every MMA issued so far (also after a failure)
             s_consumed = g;
+        }
+    } else if (V::FUSEB && warp >= V::CONV_WARP0) {
+        // Converter warps: split each stage's FP32 B tile into the three BF16
+        // planes, written K-major in the same swizzled layout a TMA load would
+        // produce (16-byte chunk c of row n at chunk c ^ ((n * SWZ / 128) & (SWZ / 16 - 1))).
+        if constexpr (V::FUSEB) {
+            const int ct = tid - 32 * V::CONV_WARP0;  // 0 .. 127
+            constexpr int KC = BK / 8;                // 16-byte chunks per plane row
+            int g = 0;
+            bool ok = true;
+            for (int i = 0; ok && i < nseg; ++i) {
+                int t, c0, c1;
+                work.seg(i, t, c0, c1);
+                const int kt_end = c1 * CKT < nkt ? c1 * CKT : nkt;
+                for (int kt = c0 * CKT; kt < kt_end; ++kt, ++g) {
+                    const int s = g % STAGES, u = g / STAGES;
+                    const bool landed = mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs);
+                    if (!__all_sync(0xffffffffu, landed)) {
+                        s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *stp = smem_raw + (sbase - raw) + s * V::STAGE_BYTES;
+                    const float *bf = reinterpret_cast<const float *>(stp + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES));
+                    unsigned char *bp = stp + P * V::A_PLANE_BYTES;
+#pragma unroll
+                    for (int it = ct; it < BN * KC; it += 32 * V::CONV_WARPS) {
+                        const int n = it % BN, kc = it / BN;
+                        float x[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[e] = bf[(kc * 8 + e) * BN + n];
+                        uint32_t b[3][4];
+#pragma unroll
+                        for (int e = 0; e < 8; e += 2) {
+                            float v0 = x[e], v1 = x[e + 1];
+#pragma unroll
+                            for (int pl = 0; pl < 3; ++pl) {
+                                const uint32_t q = bf16x2_rn(v0, v1);
+                                b[pl][e / 2] = q;
+                                v0 -= bf16_lo_f32(q);
+                                v1 -= bf16_hi_f32(q);
+                            }
+                        }
+                        const int sw = (n * V::SWZ / 128) & (V::SWZ / 16 - 1);
+                        const int off = n * V::SWZ + ((kc ^ sw) << 4);
+#pragma unroll
+                        for (int pl = 0; pl < 3; ++pl)
+                            *reinterpret_cast<uint4 *>(bp + pl * V::B_PLANE_BYTES + off) =
+                                make_uint4(b[pl][0], b[pl][1], b[pl][2], b[pl][3]);
+                    }
+                    // Generic-proxy writes become visible to the tensor core's
+                    // (async-proxy) reads before the stage is handed over.
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(conv0 + 8 * s);
+                }
+            }
         }
     } else {
         // Epilogue warps: drain each chunk's accumulator into FP32 registers,

@@ -1,0 +1,74 @@
+"""GPU: tensor-core versions that split B inside the GEMM kernel (converter
+warps write the BF16 planes into shared memory).  They must give exactly the
+bits of the version that splits B in the split kernel (same planes, same MMA
+order), stay within the FP32 bound against the oracle, handle ragged edges,
+and decline layouts they cannot read."""
+
+import numpy as np
+import pytest
+
+from oracle import gemm as og
+from oracle.checks import TOL_FP32, normalised_error
+from workloads import matrix
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+pt = pytest.importorskip("paper_2507_15277_gb300")
+
+DEV = "cuda:0"
+PAIRS = [("tcbf16x3_m128n64_p2_fb", "tcbf16x3_m128n64_p2"),
+         ("tcbf16x3_m128n64_p2_fb_sk2", "tcbf16x3_m128n64_p2"),
+         ("tcbf16x3_m128n64_p2_fb_sk4", "tcbf16x3_m128n64_p2_sk4"),
+         ("tcbf16x3_m128n64_p2_fb_stk", "tcbf16x3_m128n64_p2")]
+SHAPES = [(128, 4096, 4096), (128, 1000, 1000), (300, 200, 520), (640, 320, 2176)]
+
+
+@pytest.mark.parametrize("fused,plain", PAIRS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fused_b_matches_split_kernel_and_oracle(fused, plain, shape):
+    M, N, K = shape
+    A = matrix("uniform", 31, M, K)
+    B = matrix("uniform", 32, K, N)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    Cf = pt.sgemm(Ad, Bd, variant=pt.variant_by_name(fused))
+    Cp = pt.sgemm(Ad, Bd, variant=pt.variant_by_name(plain))
+    torch.cuda.synchronize()
+    cf = Cf.cpu().numpy()
+    if "_sk" not in fused and "_stk" not in fused and "_sk" not in plain:
+        assert np.array_equal(cf, Cp.cpu().numpy())  # identical planes and products
+    rows = np.arange(0, M, max(1, M // 64))
+    ref = og.gemm(A, B, rows=rows)
+    assert normalised_error(cf[rows], ref, K, np.abs(A).max(), np.abs(B).max()) <= TOL_FP32
+    assert pt.device_status() == 0
+
+
+@pytest.mark.parametrize("fused", [p[0] for p in PAIRS])
+def test_fused_b_integers_transposed_a_and_alpha_beta(fused):
+    M, N, K = 200, 136, 1032
+    A = matrix("ints", 41, K, M)          # stored K x M: transA = 'T'
+    B = matrix("ints", 42, K, N)
+    C0 = matrix("ints", 43, M, N)
+    ref = og.gemm(A, B, "T", "N", alpha=2.0, beta=-1.0, C=C0, M=M, N=N, K=K)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    C = torch.from_numpy(C0.copy()).to(DEV)
+    pt.sgemm(Ad, Bd, C, transA="T", alpha=2.0, beta=-1.0, variant=pt.variant_by_name(fused))
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
+
+
+def test_fused_b_declines_unreadable_b():
+    vid = pt.variant_by_name("tcbf16x3_m128n64_p2_fb")
+    A = torch.ones((128, 64), device=DEV)
+    Bt = torch.ones((96, 64), device=DEV)          # transB = 'T': B stored N x K
+    with pytest.raises(pt.PtError) as e:
+        pt.sgemm(A, Bt, transB="T", variant=vid)
+    assert e.value.code == pt._lib.PT_EUNSUPPORTED
+    Bs = torch.ones((64, 99), device=DEV)[:, :97]   # ldb = 99: rows not 16-byte aligned
+    with pytest.raises(pt.PtError) as e:
+        pt.sgemm(A, Bs, variant=vid)
+    assert e.value.code == pt._lib.PT_EUNSUPPORTED
+    # The runtime selector never needs them: pt_sgemm still runs these layouts.
+    C = pt.sgemm(A, Bt, transB="T")
+    torch.cuda.synchronize()
+    assert torch.all(C == 64.0)
