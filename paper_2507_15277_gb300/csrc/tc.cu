@@ -89,8 +89,10 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     // 8-column groups for the split kernel's vector stores).
     if (V::FUSEB && (a.tb || misaligned(a.B, 16) || a.ldb % 4 != 0))
         return set_error(PT_EUNSUPPORTED, 0, "fused-B variant needs B as K x N (transB = N), 16-byte aligned, ldb %% 4 == 0");
+    if (V::FUSEA && (a.ta || misaligned(a.A, 16) || a.lda % 4 != 0))
+        return set_error(PT_EUNSUPPORTED, 0, "fused-A variant needs A as M x K (transA = N), 16-byte aligned, lda %% 4 == 0");
     const int64_t pitch = ((int64_t)a.K + 7) / 8 * 8;
-    const int64_t a_plane = align256((int64_t)a.M * pitch * V::ELEM);
+    const int64_t a_plane = V::FUSEA ? 0 : align256((int64_t)a.M * pitch * V::ELEM);
     const int64_t b_plane = V::FUSEB ? 0 : align256((int64_t)a.N * pitch * V::ELEM);
     const int dev = current_device();
     // Grid: SPLITK == 1 is persistent, one CTA per SM (shared memory allows
@@ -134,7 +136,9 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int vb = (!misaligned(a.B, 16) && a.ldb % 4 == 0) ? 1 : 0;
     const SplitOperand oa{a.A, a.lda, a.ta, a.M, wA, a_plane, va};
     const SplitOperand ob{a.B, a.ldb, a.tb ? 0 : 1, a.N, wB, b_plane, vb};
-    const int ya = (a.M + 31) / 32, yb = V::FUSEB ? 0 : (a.N + 31) / 32;
+    // Blocks with blockIdx.y < ya split the first operand, the rest the second.
+    const int ya = V::FUSEA ? (a.N + 31) / 32 : (a.M + 31) / 32;
+    const int yb = V::FUSE ? 0 : (a.N + 31) / 32;
     cudaLaunchConfig_t scfg;
     std::memset(&scfg, 0, sizeof(scfg));
     scfg.gridDim = dim3((unsigned)((pitch + SPLIT_K_PER_BLOCK - 1) / SPLIT_K_PER_BLOCK), (unsigned)(ya + yb), 1);
@@ -145,13 +149,17 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     add_pdl_attr(sattr, nsattr);
     scfg.attrs = sattr;
     scfg.numAttrs = nsattr;
-    cudaError_t e = cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, oa, ob, (int)a.K, pitch, ya);
+    cudaError_t e = V::FUSEA ? cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, ob, ob, (int)a.K, pitch, ya)
+                             : cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, oa, ob, (int)a.K, pitch, ya);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 
     const CUtensorMapDataType dt =
         V::KIND == kTcTf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap mA, mB;
-    rc = make_map_3d(&mA, wA, dt, V::ELEM, a.K, a.M, V::P, pitch * V::ELEM, a_plane, V::BK, V::BM, V::SWZ);
+    if (V::FUSEA)
+        rc = make_map_2d(&mA, a.A, a.K, a.M, a.lda, V::BK, V::BM, CU_TENSOR_MAP_SWIZZLE_NONE);
+    else
+        rc = make_map_3d(&mA, wA, dt, V::ELEM, a.K, a.M, V::P, pitch * V::ELEM, a_plane, V::BK, V::BM, V::SWZ);
     if (rc != PT_OK) return rc;
     if (V::FUSEB)
         rc = make_map_2d(&mB, a.B, a.N, a.K, a.ldb, V::BN, V::BK, CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -211,7 +219,7 @@ VariantEntry tc_entry(const char *name) {
     v.desc.a_kmajor = 1;
     v.desc.threads = V::THREADS;
     v.desc.smem_bytes = V::SMEM_BYTES;
-    v.desc.trans_mask = V::FUSEB ? 5 : 15;  // fused B: transB = 'N' only
+    v.desc.trans_mask = V::FUSEB ? 5 : (V::FUSEA ? 3 : 15);  // fused B: transB = N only; fused A: transA = N only
     v.desc.kind = V::KIND == kTcTf32 ? 1 : 2;
     v.desc.schedule = V::STREAMK ? PT_SCHED_STREAMK : (V::SPLITK > 1 ? PT_SCHED_TILE : PT_SCHED_PERSISTENT);
     std::strncpy(v.desc.name, name, sizeof(v.desc.name) - 1);
@@ -262,6 +270,11 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcBf16x3, 64, 2, 2, 128, 0, 1>>("tcbf16x3_m128n64_p2_fb_sk2"),
         tc_entry<Tc<kTcBf16x3, 64, 2, 4, 128, 0, 1>>("tcbf16x3_m128n64_p2_fb_sk4"),
         tc_entry<Tc<kTcBf16x3, 64, 2, 1, 128, 1, 1>>("tcbf16x3_m128n64_p2_fb_stk"),
+        // Fused A split (A converted inside the GEMM kernel; small N).
+        tc_entry<Tc<kTcBf16x3, 64, 3, 1, 64, 0, 2>>("tcbf16x3_m128n64_p3_sw64_fa"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 2, 64, 0, 2>>("tcbf16x3_m128n64_p3_sw64_fa_sk2"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 4, 64, 0, 2>>("tcbf16x3_m128n64_p3_sw64_fa_sk4"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 1, 64, 1, 2>>("tcbf16x3_m128n64_p3_sw64_fa_stk"),
         // BF16x3 64-column tiles with room for the coalescing epilogue stage.
         tc_entry<Tc<kTcBf16x3, 64, 2>>("tcbf16x3_m128n64_p2"),
         tc_entry<Tc<kTcBf16x3, 64, 2, 4>>("tcbf16x3_m128n64_p2_sk4"),

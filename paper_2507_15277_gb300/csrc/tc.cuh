@@ -48,7 +48,7 @@
 
 namespace pt {
 
-template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128, int STREAMK_ = 0, int FUSEB_ = 0>
+template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128, int STREAMK_ = 0, int FUSE_ = 0>
 struct Tc {
     static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_, SPLITK = SPLITK_;
     // Stream-K (SPLITK == 1 only): the grid's CTAs split tiles x chunks into
@@ -57,12 +57,14 @@ struct Tc {
     // its last chunk, which adds the others' FP32 partial tiles.
     static constexpr int STREAMK = STREAMK_;
     static_assert(STREAMK == 0 || SPLITK == 1, "stream-K replaces split-K");
-    // Fused B split (BF16x3, B stored K x N with N contiguous): the producer
-    // loads FP32 tiles of B itself and four converter warps write its three
-    // planes into the stage, so B never passes through the split kernel.
-    // Pays where B dominates the traffic (small M).
-    static constexpr int FUSEB = FUSEB_;
-    static_assert(FUSEB == 0 || KIND_ == 1, "fused B split is BF16x3 only");
+    // Fused split (BF16x3): the producer loads FP32 tiles of one operand
+    // itself and four converter warps write its three planes into the stage,
+    // so that operand never passes through the split kernel.  FUSE = 1: B
+    // (stored K x N, N contiguous; pays for small M); FUSE = 2: A (stored
+    // M x K, K contiguous; pays for small N).
+    static constexpr int FUSE = FUSE_;
+    static constexpr bool FUSEB = FUSE == 1, FUSEA = FUSE == 2;
+    static_assert(FUSE == 0 || KIND_ == 1, "fused split is BF16x3 only");
     // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
     // A narrower row makes the stage smaller, so more stages fit and the
     // producer refills a smaller part of the pipeline at a time.
@@ -85,14 +87,17 @@ struct Tc {
     static constexpr int CHUNK_KT = 128 / BK;
     static constexpr int A_PLANE_BYTES = BM * SWZ;
     static constexpr int B_PLANE_BYTES = BN * SWZ;
-    static constexpr int BF32_BYTES = FUSEB ? BK * BN * 4 : 0;  // FP32 B tile [BK][BN]
-    static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES) + BF32_BYTES;
-    static constexpr int LOAD_BYTES = FUSEB ? P * A_PLANE_BYTES + BF32_BYTES : STAGE_BYTES;  // TMA bytes
+    // FP32 tile of the fused operand: B as [BK][BN], A as [BM][BK].
+    static constexpr int F32_BYTES = FUSEB ? BK * BN * 4 : (FUSEA ? BM * BK * 4 : 0);
+    static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES) + F32_BYTES;
+    static constexpr int LOAD_BYTES = FUSEB   ? P * A_PLANE_BYTES + F32_BYTES
+                                      : FUSEA ? P * B_PLANE_BYTES + F32_BYTES
+                                              : STAGE_BYTES;  // bytes the TMA loads deliver per stage
     static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
     // Barriers (full, empty per stage; converted per stage when FUSEB; two
     // accumulator-full, two accumulator-empty, MMA-done) and the TMEM address
     // slot.
-    static constexpr int BAR_BYTES = 8 * ((FUSEB ? 3 : 2) * STAGES + 6);
+    static constexpr int BAR_BYTES = 8 * ((FUSE ? 3 : 2) * STAGES + 6);
 
     // Accumulator buffer: 2*BN columns (left half, right half); two buffers.
     static constexpr int ACC_COLS = 2 * BN;
@@ -103,7 +108,7 @@ struct Tc {
     static constexpr int COLS = BN / COL_GROUPS;
     static constexpr int EPI_WARPS = 4 * COL_GROUPS;
     static constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
-    static constexpr int CONV_WARP0 = EPI_WARPS + 2, CONV_WARPS = FUSEB ? 4 : 0;
+    static constexpr int CONV_WARP0 = EPI_WARPS + 2, CONV_WARPS = FUSE ? 4 : 0;
     static constexpr int THREADS = 32 * (EPI_WARPS + 2 + CONV_WARPS);
     // Epilogue staging (when it fits): each epilogue warp transposes its 32
     // rows through a 32 x STG_LD float buffer, 32 columns at a time, so that
@@ -257,8 +262,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     const uint32_t sbase = (raw + 1023u) & ~1023u;
     const uint32_t full0 = sbase + V::BAR_OFFSET;  // STAGES: TMA landed
     const uint32_t empty0 = full0 + 8 * STAGES;    // STAGES: MMAs done reading
-    const uint32_t conv0 = empty0 + 8 * STAGES;    // STAGES (FUSEB): B planes written
-    const uint32_t accf0 = conv0 + (V::FUSEB ? 8 * STAGES : 0);  // 2: accumulator buffer ready
+    const uint32_t conv0 = empty0 + 8 * STAGES;    // STAGES (FUSE): fused operand's planes written
+    const uint32_t accf0 = conv0 + (V::FUSE ? 8 * STAGES : 0);  // 2: accumulator buffer ready
     const uint32_t acce0 = accf0 + 16;             // 2: accumulator buffer drained
     const uint32_t doneb = acce0 + 16;             // every issued MMA finished
     const uint32_t tslot = doneb + 8;
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
-            if (V::FUSEB) mbar_init(conv0 + 8 * s, V::CONV_WARPS);
+            if (V::FUSE) mbar_init(conv0 + 8 * s, V::CONV_WARPS);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf0 + 8 * b, 1);
@@ -349,9 +354,15 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     }
                     const uint32_t st = sbase + s * V::STAGE_BYTES;
                     mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::LOAD_BYTES);
+                    if constexpr (V::FUSEA) {
+                        // FP32 tile of A: BM rows, BK columns of k (2-D map over A itself).
+                        tma_load_2d(st + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES), &mapA, full0 + 8 * s,
+                                    (kt0 + kt) * BK, m0);
+                    } else {
 #pragma unroll
-                    for (int p = 0; p < P; ++p)
-                        tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, (kt0 + kt) * BK, m0, p);
+                        for (int p = 0; p < P; ++p)
+                            tma_load_3d(st + p * V::A_PLANE_BYTES, &mapA, full0 + 8 * s, (kt0 + kt) * BK, m0, p);
+                    }
                     if constexpr (V::FUSEB) {
                         // FP32 tile of B: BK rows of k, BN columns of n (2-D map over B itself).
                         tma_load_2d(st + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES), &mapB, full0 + 8 * s, n0,
@@ -387,7 +398,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         }
                     }
                     if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs) ||
-                        (V::FUSEB && !mbar_wait_bounded(conv0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs))) {
+                        (V::FUSE && !mbar_wait_bounded(conv0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs))) {
                         s_fail = 1;
                         ok = false;
                         break;
@@ -419,11 +430,12 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             tc_commit(doneb);  // every MMA issued so far (also after a failure)
             s_consumed = g;
         }
-    } else if (V::FUSEB && warp >= V::CONV_WARP0) {
-        // Converter warps: split each stage's FP32 B tile into the three BF16
-        // planes, written K-major in the same swizzled layout a TMA load would
-        // produce (16-byte chunk c of row n at chunk c ^ ((n * SWZ / 128) & (SWZ / 16 - 1))).
-        if constexpr (V::FUSEB) {
+    } else if (V::FUSE && warp >= V::CONV_WARP0) {
+        // Converter warps: split each stage's FP32 tile of the fused operand
+        // into the three BF16 planes, written K-major in the same swizzled
+        // layout a TMA load would produce (16-byte chunk c of plane row r at
+        // chunk c ^ ((r * SWZ / 128) & (SWZ / 16 - 1))).
+        if constexpr (V::FUSE) {
             const int ct = tid - 32 * V::CONV_WARP0;  // 0 .. 127
             constexpr int KC = BK / 8;                // 16-byte chunks per plane row
             int g = 0;
@@ -442,13 +454,25 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     }
                     unsigned char *stp = smem_raw + (sbase - raw) + s * V::STAGE_BYTES;
                     const float *bf = reinterpret_cast<const float *>(stp + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES));
-                    unsigned char *bp = stp + P * V::A_PLANE_BYTES;
+                    unsigned char *bp = stp + (V::FUSEB ? P * V::A_PLANE_BYTES : 0);
+                    constexpr int ROWS = V::FUSEB ? BN : V::BM;  // plane rows of the fused operand
+                    constexpr int PLANE = V::FUSEB ? V::B_PLANE_BYTES : V::A_PLANE_BYTES;
 #pragma unroll
-                    for (int it = ct; it < BN * KC; it += 32 * V::CONV_WARPS) {
-                        const int n = it % BN, kc = it / BN;
+                    for (int it = ct; it < ROWS * KC; it += 32 * V::CONV_WARPS) {
+                        // B: lanes take consecutive n of one k chunk (the FP32
+                        // tile is [k][n]); A: KC lanes share a row, so a warp
+                        // reads whole rows of the [m][k] tile.
+                        const int n = V::FUSEB ? it % ROWS : it / KC, kc = V::FUSEB ? it / ROWS : it % KC;
                         float x[8];
+                        if constexpr (V::FUSEB) {
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) x[e] = bf[(kc * 8 + e) * BN + n];
+                            for (int e = 0; e < 8; ++e) x[e] = bf[(kc * 8 + e) * BN + n];
+                        } else {
+                            const float4 lo = *reinterpret_cast<const float4 *>(bf + n * BK + kc * 8);
+                            const float4 hi = *reinterpret_cast<const float4 *>(bf + n * BK + kc * 8 + 4);
+                            x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+                            x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+                        }
                         uint32_t b[3][4];
 #pragma unroll
                         for (int e = 0; e < 8; e += 2) {
@@ -465,7 +489,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         const int off = n * V::SWZ + ((kc ^ sw) << 4);
 #pragma unroll
                         for (int pl = 0; pl < 3; ++pl)
-                            *reinterpret_cast<uint4 *>(bp + pl * V::B_PLANE_BYTES + off) =
+                            *reinterpret_cast<uint4 *>(bp + pl * PLANE + off) =
                                 make_uint4(b[pl][0], b[pl][1], b[pl][2], b[pl][3]);
                     }
                     // Generic-proxy writes become visible to the tensor core's

@@ -1,8 +1,8 @@
-"""GPU: tensor-core versions that split B inside the GEMM kernel (converter
-warps write the BF16 planes into shared memory).  They must give exactly the
-bits of the version that splits B in the split kernel (same planes, same MMA
-order), stay within the FP32 bound against the oracle, handle ragged edges,
-and decline layouts they cannot read."""
+"""GPU: tensor-core versions that split B (or A) inside the GEMM kernel
+(converter warps write the BF16 planes into shared memory).  They must give
+exactly the bits of the version that splits both operands in the split
+kernel (same planes, same MMA order), stay within the FP32 bound against the
+oracle, handle ragged edges, and decline layouts they cannot read."""
 
 import numpy as np
 import pytest
@@ -72,3 +72,53 @@ def test_fused_b_declines_unreadable_b():
     C = pt.sgemm(A, Bt, transB="T")
     torch.cuda.synchronize()
     assert torch.all(C == 64.0)
+
+
+PAIRS_A = [("tcbf16x3_m128n64_p3_sw64_fa", "tcbf16x3_m128n64_p4_sw64"),
+           ("tcbf16x3_m128n64_p3_sw64_fa_sk2", "tcbf16x3_m128n64_p4_sw64"),
+           ("tcbf16x3_m128n64_p3_sw64_fa_sk4", "tcbf16x3_m128n64_p4_sw64_sk4"),
+           ("tcbf16x3_m128n64_p3_sw64_fa_stk", "tcbf16x3_m128n64_p4_sw64")]
+SHAPES_A = [(4096, 128, 4096), (1000, 128, 1000), (300, 200, 520), (640, 320, 2176)]
+
+
+@pytest.mark.parametrize("fused,plain", PAIRS_A)
+@pytest.mark.parametrize("shape", SHAPES_A)
+def test_fused_a_matches_split_kernel_and_oracle(fused, plain, shape):
+    M, N, K = shape
+    A = matrix("uniform", 51, M, K)
+    B = matrix("uniform", 52, K, N)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    Cf = pt.sgemm(Ad, Bd, variant=pt.variant_by_name(fused))
+    Cp = pt.sgemm(Ad, Bd, variant=pt.variant_by_name(plain))
+    torch.cuda.synchronize()
+    cf = Cf.cpu().numpy()
+    if "_sk" not in fused and "_stk" not in fused:
+        # same planes and the same k-chunk order (stage depth does not change the arithmetic)
+        assert np.array_equal(cf, Cp.cpu().numpy())
+    rows = np.arange(0, M, max(1, M // 64))
+    ref = og.gemm(A, B, rows=rows)
+    assert normalised_error(cf[rows], ref, K, np.abs(A).max(), np.abs(B).max()) <= TOL_FP32
+    assert pt.device_status() == 0
+
+
+@pytest.mark.parametrize("fused", [p[0] for p in PAIRS_A])
+def test_fused_a_integers_transposed_b_and_alpha_beta(fused):
+    M, N, K = 200, 136, 1032
+    A = matrix("ints", 61, M, K)
+    B = matrix("ints", 62, N, K)          # stored N x K: transB = 'T'
+    C0 = matrix("ints", 63, M, N)
+    ref = og.gemm(A, B, "N", "T", alpha=2.0, beta=-1.0, C=C0, M=M, N=N, K=K)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    C = torch.from_numpy(C0.copy()).to(DEV)
+    pt.sgemm(Ad, Bd, C, transB="T", alpha=2.0, beta=-1.0, variant=pt.variant_by_name(fused))
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
+
+
+def test_fused_a_declines_unreadable_a():
+    vid = pt.variant_by_name("tcbf16x3_m128n64_p3_sw64_fa")
+    At = torch.ones((64, 128), device=DEV)          # transA = 'T': A stored K x M
+    B = torch.ones((64, 96), device=DEV)
+    with pytest.raises(pt.PtError) as e:
+        pt.sgemm(At, B, transA="T", variant=vid)
+    assert e.value.code == pt._lib.PT_EUNSUPPORTED

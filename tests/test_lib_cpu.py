@@ -49,10 +49,11 @@ def test_registry_rules():
         if d["kind"] != 0:
             # split-precision tensor-core variants: 128-row tiles, TMA, any layout
             assert d["kind"] in (1, 2) and d["bm"] == 128 and d["bn"] in (64, 128)
-            # fused-B versions read B itself (transB = 'N' only); the others take any layout
-            assert d["loader"] == 1 and d["trans_mask"] == (5 if "_fb" in d["name"] else 15)
+            # fused versions read B (or A) themselves: transB (transA) = 'N' only; the others take any layout
+            assert d["loader"] == 1 and d["trans_mask"] == (5 if "_fb" in d["name"] else 3 if "_fa" in d["name"] else 15)
             # epilogue + producer + MMA warps (+ four converter warps when B is split in the kernel)
-            assert d["threads"] == 32 * (4 * max(1, d["bn"] // 128) + 2 + (4 if "_fb" in d["name"] else 0))
+            fused = "_fb" in d["name"] or "_fa" in d["name"]
+            assert d["threads"] == 32 * (4 * max(1, d["bn"] // 128) + 2 + (4 if fused else 0))
             want = (pt.PT_SCHED_STREAMK if d["name"].endswith("_stk") else
                     pt.PT_SCHED_TILE if d["splitk"] > 1 else pt.PT_SCHED_PERSISTENT)
             assert d["schedule"] == want
