@@ -12,12 +12,18 @@
 // |a*b|, so the result is FP32-accurate; these variants join the FP32 SIMT
 // family as further versions of the same operation.
 //
-// Pipeline (a persistent CTA per SM walks the 128 x BN output tiles; split-K
+// Pipeline (a persistent CTA per SM walks the 128 x BN output tiles;
+// stream-K versions share the last waves' tiles in 128-k chunks; split-K
 // versions: one tile per cluster):
 //   a split kernel writes the planes K-major into the library workspace;
 //   producer warp (one lane): TMA loads of every plane's tile (3-D tensor maps
-//                  over [plane][row][k], 128-byte swizzle), full/empty
-//                  mbarriers per stage;
+//                  over [plane][row][k], 128/64/32-byte swizzle), full/empty
+//                  mbarriers per stage; fused versions load the FP32 tile of
+//                  one operand instead (2-D map over the operand itself);
+//   converter warps (fused versions only): split that FP32 tile into the
+//                  operand's three BF16 planes in the stage, in the layout a
+//                  swizzled TMA load would give, then hand the stage to the
+//                  MMA warp;
 //   MMA warp (one lane): tcgen05.mma (cta_group::1, M = 128, A and B
 //                  K-major from shared-memory descriptors) into one of two
 //                  TMEM accumulators; every 128 values of k (a "chunk") the
@@ -35,7 +41,8 @@
 //                  registers with IEEE round-to-nearest ("promotion": the
 //                  tensor core's own accumulation, which is not IEEE
 //                  round-to-nearest, then spans only 128 products),
-//                  alpha/beta, stores to C.
+//                  alpha/beta, coalesced stores to C through a small
+//                  per-warp staging buffer.
 // Every mbarrier wait is bounded; tensor memory is always freed.
 #pragma once
 
