@@ -55,11 +55,12 @@ def parse():
     p.add_argument("--single", default=None, metavar="M,N,K",
                    help="profiling mode: run one variant (--variant) on one shape, no tuning")
     p.add_argument("--variant", default=None, help="variant name for --single")
-    p.add_argument("--report", default=None, choices=["splitprec", "grouped", "stability", "oracle"],
+    p.add_argument("--report", default=None, choices=["splitprec", "grouped", "stability", "oracle", "autograd"],
                    help="splitprec: tensor-core split-precision vs FP32 SIMT on the split-precision shapes; "
                         "grouped: 512 uneven problems, persistent grouped launch vs separate launches; "
                         "stability: the sweep tuned twice, rank agreement of the two timing tables; "
-                        "oracle: the FP64 CPU oracle timed at 256^3, 1024^3 and 4096^3")
+                        "oracle: the FP64 CPU oracle timed at 256^3, 1024^3 and 4096^3; "
+                        "autograd: Y = X W forward and backward through the tuned SGEMM")
     return p.parse_args()
 
 
@@ -313,6 +314,89 @@ def report_oracle(args):
     return 0
 
 
+def report_autograd(args):
+    """Y = X W with X[4096,1024], W[1024,4096] ~ N(0, 0.02^2), G ~ N(0,1)
+    (seed 4): the three products (NN forward, NT dX = G W^T, TN dW = X^T G)
+    are tuned over every variant, k = 3 are selected on them, and forward +
+    backward through the autograd Function is timed against torch.matmul in
+    FP32 (TF32 off); errors of Y, dX, dW against the FP64 oracle on sampled
+    rows."""
+    import numpy as np
+    import torch
+
+    import paper_2507_15277_gb300 as pt
+    from oracle import gemm as og
+    from oracle.checks import normalised_error
+    from paper_2507_15277_gb300.autograd import matmul
+    from workloads import matrix
+    dev = torch.device("cuda", 0)
+    Mx, Kx, Nw = 4096, 1024, 4096
+    X = matrix("normal", 4, Mx, Kx, std=0.02)
+    W = matrix("normal", 104, Kx, Nw, std=0.02)
+    G = matrix("normal", 204, Mx, Nw)
+    shapes = [(Mx, Nw, Kx, "N", "N"), (Mx, Kx, Nw, "N", "T"), (Kx, Nw, Mx, "T", "N")]
+    out_dir = args.out_dir or tempfile.mkdtemp(prefix="ptgrad_")
+    os.makedirs(out_dir, exist_ok=True)
+    table = os.path.join(out_dir, "autograd_table.csv")
+    pt.tune(shapes, table, reps_min=3, reps_max=10, target_ms=5.0)
+    manifest = os.path.join(out_dir, "autograd_k3.json")
+    ids, _ = pt.select(table, [0, 1, 2], 3, manifest=manifest)
+    pt.load_manifest(manifest)
+    Xd = torch.from_numpy(X).to(dev).requires_grad_(True)
+    Wd = torch.from_numpy(W).to(dev).requires_grad_(True)
+    Gd = torch.from_numpy(G).to(dev)
+
+    def ours():
+        Y = matmul(Xd, Wd)
+        Y.backward(Gd)
+        return Y
+
+    def ref():
+        Y = torch.matmul(Xd, Wd)
+        Y.backward(Gd)
+        return Y
+
+    torch.backends.cuda.matmul.allow_tf32 = False
+    torch.set_float32_matmul_precision("highest")
+    res = {}
+    for name, fn in (("pt_sgemm", ours), ("torch_fp32", ref)):
+        for _ in range(3):
+            Xd.grad = None
+            Wd.grad = None
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            Xd.grad = None
+            Wd.grad = None
+            Y = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        res[name] = {"ms": ms, "tflops": 3 * 2.0 * Mx * Nw * Kx / (ms * 1e-3) / 1e12}
+    Xd.grad = None
+    Wd.grad = None
+    Y = ours()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    rx = np.sort(rng.choice(Mx, 64, replace=False))
+    rw = np.sort(rng.choice(Kx, 64, replace=False))
+    err = {
+        "Y": normalised_error(Y.detach()[rx].cpu().numpy(), og.gemm(X, W, rows=rx), Kx, np.abs(X).max(),
+                              np.abs(W).max()),
+        "dX": normalised_error(Xd.grad[rx].cpu().numpy(), og.gemm(G, W, "N", "T", rows=rx), Nw, np.abs(G).max(),
+                               np.abs(W).max()),
+        "dW": normalised_error(Wd.grad[rw].cpu().numpy(), og.gemm(X, G, "T", "N", rows=rw), Mx, np.abs(X).max(),
+                               np.abs(G).max()),
+    }
+    print(json.dumps({"mode": "autograd", "shapes": [list(s[:3]) + [s[3] + s[4]] for s in shapes],
+                      "kappa": [pt.variant(i)["name"] for i in ids],
+                      "picks": [pt.variant(pt.selected_variant(m, n, k, ta, tb))["name"] for m, n, k, ta, tb in shapes],
+                      "timing": res, "errors": err}))
+    return 0
+
+
 def single(args):
     """One variant on one shape, `warmup` + `steps` launches (for ncu captures)."""
     import torch
@@ -549,6 +633,8 @@ def main():
         return report_stability(args)
     if args.report == "oracle":
         return report_oracle(args)
+    if args.report == "autograd":
+        return report_autograd(args)
 
     import numpy as np
     import torch
