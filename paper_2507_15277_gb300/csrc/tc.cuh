@@ -115,7 +115,10 @@ struct Tc {
     static constexpr int COLS = BN / COL_GROUPS;
     static constexpr int EPI_WARPS = 4 * COL_GROUPS;
     static constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
-    static constexpr int CONV_WARP0 = EPI_WARPS + 2, CONV_WARPS = FUSE ? 4 : 0;
+    // Converter warps: four for 64-column tiles; two for 128-column tiles,
+    // whose epilogue threads need the larger per-thread register budget of a
+    // 256-thread CTA.
+    static constexpr int CONV_WARP0 = EPI_WARPS + 2, CONV_WARPS = FUSE ? (BN >= 128 ? 2 : 4) : 0;
     static constexpr int THREADS = 32 * (EPI_WARPS + 2 + CONV_WARPS);
     // Epilogue staging (when it fits): each epilogue warp transposes its 32
     // rows through a 32 x STG_LD float buffer, 32 columns at a time, so that
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         // layout a TMA load would produce (16-byte chunk c of plane row r at
         // chunk c ^ ((r * SWZ / 128) & (SWZ / 16 - 1))).
         if constexpr (V::FUSE) {
-            const int ct = tid - 32 * V::CONV_WARP0;  // 0 .. 127
+            const int ct = tid - 32 * V::CONV_WARP0;  // 0 .. 32 * CONV_WARPS - 1
             constexpr int KC = BK / 8;                // 16-byte chunks per plane row
             int g = 0;
             bool ok = true;

@@ -53,7 +53,8 @@ def test_registry_rules():
             assert d["loader"] == 1 and d["trans_mask"] == (5 if "_fb" in d["name"] else 3 if "_fa" in d["name"] else 15)
             # epilogue + producer + MMA warps (+ four converter warps when B is split in the kernel)
             fused = "_fb" in d["name"] or "_fa" in d["name"]
-            assert d["threads"] == 32 * (4 * max(1, d["bn"] // 128) + 2 + (4 if fused else 0))
+            conv = (2 if d["bn"] >= 128 else 4) if fused else 0  # converter warps
+            assert d["threads"] == 32 * (4 * max(1, d["bn"] // 128) + 2 + conv)
             want = (pt.PT_SCHED_STREAMK if d["name"].endswith("_stk") else
                     pt.PT_SCHED_TILE if d["splitk"] > 1 else pt.PT_SCHED_PERSISTENT)
             assert d["schedule"] == want
