@@ -26,7 +26,7 @@ from ._lib import (PT_LOADER_CPASYNC, PT_LOADER_TMA, PT_SCHED_PERSISTENT,  # noq
 __all__ = [
     "sgemm", "reference", "num_variants", "variant", "variants", "variant_by_name", "default_variant",
     "tune", "select", "score", "table_shapes", "load_manifest", "selected_variant", "device_status",
-    "grouped_problems", "upload_problems", "sgemm_grouped", "kernel_timer_start", "kernel_timer_stop",
+    "grouped_problems", "upload_problems", "sgemm_grouped", "kernel_timer_start", "kernel_timer_stop", "shutdown",
     "PtError",
 ]
 
@@ -146,6 +146,11 @@ def selected_variant(M: int, N: int, K: int, transA: str = "N", transB: str = "N
 
 def device_status() -> int:
     return _l().pt_device_status()
+
+
+def shutdown() -> None:
+    """Frees the library's device workspaces and unloads the manifest."""
+    _lib.check(_l().pt_shutdown(), "pt_shutdown")
 
 
 def kernel_timer_start() -> None:

@@ -89,3 +89,17 @@ def test_streamk_alpha_beta():
         e = normalised_error(C.cpu().numpy(), ref, K, amax, bmax, alpha=0.75, beta=-1.25,
                              maxC=float(np.abs(C0).max()))
         assert e <= TOL_FP32, name
+
+
+def test_streamk_after_shutdown_recreates_workspace():
+    # pt_shutdown frees the workspaces (and their stream-K flags); the next
+    # call allocates a fresh, zeroed one and must still be exact.
+    M, N, K = 1024, 1024, 4096
+    A, B, ref, _, _ = _ref("ints", M, N, K)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    vid = pt.variant_by_name(STK[0])
+    for _ in range(2):
+        C = pt.sgemm(Ad, Bd, variant=vid)
+        torch.cuda.synchronize()
+        assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
+        pt.shutdown()
