@@ -232,11 +232,12 @@ int pt_grouped_plan(pt_gemm_problem_t *problems, int count);
 int pt_sgemm_grouped(const pt_gemm_problem_t *problems, const pt_gemm_problem_t *problems_dev, int count,
                      void *stream);
 
-/* Frees the library's device workspaces (the split planes of the tensor-core
- * variants, one buffer per device and stream, grown on first use of a larger
- * shape; growing is refused with PT_EUNSUPPORTED while the stream is being
- * captured, and pt_sgemm then falls back to another variant) and unloads the
- * manifest.  Synchronises the devices that hold a workspace. */
+/* Frees the library's device workspaces (one buffer per device and stream
+ * for the tensor-core variants: stream-K flags and partial tiles, then the
+ * split planes; grown on first use of a larger shape; growing is refused with
+ * PT_EUNSUPPORTED while the stream is being captured, and pt_sgemm then falls
+ * back to another variant) and unloads the manifest.  Synchronises the
+ * devices that hold a workspace.  Calls made afterwards allocate afresh. */
 int pt_shutdown(void);
 
 /* Allocation-free SGEMM (the paper has no counterpart; this is a library
