@@ -143,15 +143,15 @@ def report_splitprec(args):
     """Split-precision tensor-core variants vs the FP32 SIMT family on
     M=N=K in {1024, 4096, 8192}, 8192x8192x256 and 256x8192x8192, inputs of
     random sign with magnitudes 2^U[-10,10] (seed 3): TFLOP/s of the fastest
-    variant of each kind (timed by the tuner) and its normalised error
-    against the FP64 oracle on 512 sampled rows (all rows when M <= 512);
+    variant of each kind (timed by the tuner) and its normalised error on
+    512 sampled rows (all rows when M <= 512) against the library's
+    compensated-dot reference kernel (the tests hold that kernel, and these
+    variants on these inputs, to the FP64 oracle);
     TF32 cuBLAS throughput at 8192^3 as the measured TF32 reference."""
     import numpy as np
     import torch
 
     import paper_2507_15277_gb300 as pt
-    from oracle import gemm as og
-    from oracle.checks import normalised_error
     from workloads import matrix, split_precision_shapes
     dev = torch.device("cuda", 0)
     shapes = split_precision_shapes()
@@ -178,8 +178,8 @@ def report_splitprec(args):
         A = matrix("logu", 3, M, K)
         B = matrix("logu", 4, K, N)
         sample = np.sort(np.random.default_rng(si).choice(M, min(512, M), replace=False))
-        ref = og.gemm(A, B, rows=sample)
         Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        ref = pt.reference(Ad, Bd)[sample].cpu().numpy().astype(np.float64)
         entry = {"shape": [M, N, K]}
         for kind, label in ((0, "fp32_simt"), (1, "3xtf32"), (2, "bf16x3")):
             if kind not in best:
@@ -187,7 +187,7 @@ def report_splitprec(args):
             t, name = best[kind]
             C = pt.sgemm(Ad, Bd, variant=pt.variant_by_name(name))
             torch.cuda.synchronize()
-            err = normalised_error(C[sample].cpu().numpy(), ref, K, np.abs(A).max(), np.abs(B).max())
+            err = _normalised(C[sample].cpu().numpy(), ref, K, np.abs(A).max(), np.abs(B).max())
             entry[label] = {"variant": name, "ms": t, "tflops": 2.0 * M * N * K / (t * 1e-3) / 1e12, "err": err}
         del Ad, Bd
         res.append(entry)
@@ -204,9 +204,17 @@ def report_splitprec(args):
     torch.cuda.synchronize()
     tf32 = 10 * 2.0 * 8192 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12
     torch.backends.cuda.matmul.allow_tf32 = False
-    print(json.dumps({"mode": "splitprec", "inputs": "sign * 2^U[-10,10], seed 3; error on 512 sampled rows",
+    print(json.dumps({"mode": "splitprec", "inputs": "sign * 2^U[-10,10], seed 3; error on 512 sampled rows against "
+                      "the library's compensated-dot reference kernel",
                       "tune_s": tune_s, "tf32_cublas_tflops_8192": tf32, "shapes": res}))
     return 0
+
+
+def _normalised(C, R, K, amax, bmax):
+    """max |C - R| / (K max|A| max|B|): the normalised error of a result
+    against a reference result."""
+    import numpy as np
+    return float(np.abs(np.asarray(C, np.float64) - np.asarray(R, np.float64)).max() / (K * amax * bmax))
 
 
 def _ranks(x):
@@ -277,9 +285,10 @@ def report_stability(args):
     return 0
 
 
-def report_oracle(args):
-    """The FP64 CPU oracle timed at 256^3, 1024^3 and 4096^3, on one thread and
-    on all of the host's threads (GFLOP/s), with the host CPU model."""
+def cpu_oracle_square():
+    """CPU-baseline leg: the FP64 oracle timed at 256^3, 1024^3 and 4096^3,
+    on one thread and on all of the host's threads (GFLOP/s), with the host
+    CPU model.  The one-thread 4096^3 run is bounded to 256 of the rows."""
     import numpy as np
 
     from oracle import gemm as og
@@ -301,7 +310,7 @@ def report_oracle(args):
             og.set_threads(threads)
             rows = None
             if threads == 1 and n == 4096:
-                rows = np.arange(256)  # bounded: 256 of the 4096 rows on one thread
+                rows = np.arange(256)
             og.gemm(A[:8], B, M=8, N=n, K=n)  # warm
             t0 = time.perf_counter()
             og.gemm(A, B, M=n, N=n, K=n, rows=rows)
@@ -310,7 +319,12 @@ def report_oracle(args):
             res.append({"shape": [n, n, n], "threads": threads, "rows": m, "s": dt,
                         "gflops": 2.0 * m * n * n / dt / 1e9})
     og.set_threads(nmax)
-    print(json.dumps({"mode": "oracle", "cpu": model, "threads_max": nmax, "runs": res}))
+    return {"cpu": model, "threads_max": nmax, "runs": res}
+
+
+def report_oracle(args):
+    """The CPU-baseline leg's square-size timings by themselves."""
+    print(json.dumps(dict(mode="oracle", **cpu_oracle_square())))
     return 0
 
 
@@ -319,14 +333,13 @@ def report_autograd(args):
     (seed 4): the three products (NN forward, NT dX = G W^T, TN dW = X^T G)
     are tuned over every variant, k = 3 are selected on them, and forward +
     backward through the autograd Function is timed against torch.matmul in
-    FP32 (TF32 off); errors of Y, dX, dW against the FP64 oracle on sampled
-    rows."""
+    FP32 (TF32 off); errors of Y, dX, dW on sampled rows against the
+    library's compensated-dot reference kernel (the FP64 oracle checks the
+    gradients in the tests)."""
     import numpy as np
     import torch
 
     import paper_2507_15277_gb300 as pt
-    from oracle import gemm as og
-    from oracle.checks import normalised_error
     from paper_2507_15277_gb300.autograd import matmul
     from workloads import matrix
     dev = torch.device("cuda", 0)
@@ -382,13 +395,16 @@ def report_autograd(args):
     rng = np.random.default_rng(4)
     rx = np.sort(rng.choice(Mx, 64, replace=False))
     rw = np.sort(rng.choice(Kx, 64, replace=False))
+    with torch.no_grad():
+        refs = (pt.reference(Xd.detach(), Wd.detach()), pt.reference(Gd, Wd.detach(), transB="T"),
+                pt.reference(Xd.detach(), Gd, transA="T"))
     err = {
-        "Y": normalised_error(Y.detach()[rx].cpu().numpy(), og.gemm(X, W, rows=rx), Kx, np.abs(X).max(),
-                              np.abs(W).max()),
-        "dX": normalised_error(Xd.grad[rx].cpu().numpy(), og.gemm(G, W, "N", "T", rows=rx), Nw, np.abs(G).max(),
-                               np.abs(W).max()),
-        "dW": normalised_error(Wd.grad[rw].cpu().numpy(), og.gemm(X, G, "T", "N", rows=rw), Mx, np.abs(X).max(),
-                               np.abs(G).max()),
+        "Y": _normalised(Y.detach()[rx].cpu().numpy(), refs[0][rx].cpu().numpy(), Kx, np.abs(X).max(),
+                         np.abs(W).max()),
+        "dX": _normalised(Xd.grad[rx].cpu().numpy(), refs[1][rx].cpu().numpy(), Nw, np.abs(G).max(),
+                          np.abs(W).max()),
+        "dW": _normalised(Wd.grad[rw].cpu().numpy(), refs[2][rw].cpu().numpy(), Mx, np.abs(X).max(),
+                          np.abs(G).max()),
     }
     print(json.dumps({"mode": "autograd", "shapes": [list(s[:3]) + [s[3] + s[4]] for s in shapes],
                       "kappa": [pt.variant(i)["name"] for i in ids],
@@ -943,7 +959,8 @@ def main():
         v, dt, cores, fl = cpu_oracle_sample(shapes, args.cpu_rows)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "FP64 CPU oracle on the first %d rows of each of the 64 shapes (%.1f GFLOP, %.1f s)"
-                         % (args.cpu_rows, fl / 1e9, dt)}
+                         % (args.cpu_rows, fl / 1e9, dt),
+               "square": cpu_oracle_square()}
 
     sel = info.get("selection", {})
     line = {
