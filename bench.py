@@ -971,6 +971,8 @@ def main():
                    "train_split": "parity (i_m+i_n+i_k even) 32/32",
                    "l2": "inputs 1.6 GB (> 129 MB L2) read once per step; no flush needed",
                    "timed": "CUDA graph of the 64 pt_sgemm launches, replayed per step",
+                   "compute": "FP32 operands and results; FP32 FMA (SIMT variants) or BF16x3 / 3xTF32 tensor-core "
+                              "splits with FP32 accumulation, whichever the selector picks per shape",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "clocks": clk,
         "gpu_launches": args.steps * sum(1 if pt.variant(p)["kind"] == 0 else 2 for p in picks),
