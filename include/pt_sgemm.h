@@ -165,7 +165,8 @@ int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids,
 /* PortabilityTune (Section IV-B, cost Eq. 1): choose kappa, |kappa| <= k, of
  * table variants maximising the geometric mean over the training shapes
  * (indices into the table's distinct-shape list, in order of first
- * appearance) of t_best(s) / min_{v in kappa} t(v, s), t_best over every
+ * appearance; n_train == 0 trains on every shape of the table) of
+ * t_best(s) / min_{v in kappa} t(v, s), t_best over every
  * valid variant of the table.  Writes the ids to out_ids[0..k) (-1 padded),
  * the training geomean to *out_train_geomean, and, when manifest_path is not
  * NULL, a manifest (kappa + each training shape's fastest member).  `seed`
