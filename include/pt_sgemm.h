@@ -52,7 +52,12 @@ int pt_last_error_arg(void);
  * "classifier" of the paper's Fig. 1, Section III-C) maps the call's
  * (transA, transB, M, N, K) to one variant of the loaded set kappa
  * (pt_load_manifest): an exact shape hit takes the member timed fastest on
- * that shape; any other shape takes the pick of the nearest listed shape in
+ * that shape.  Any other shape goes, in this order, to the manifest's
+ * regression tree (PT_SELECT_TREE manifests), else to its time model (one
+ * least-squares quadratic in (log2 M, log2 N, log2 K) of ln t per member,
+ * fitted on the training shapes when they share one transpose pair and used
+ * only for queries with that pair: the member of least predicted time, ties
+ * to the earlier member), else to the pick of the nearest listed shape in
  * (log2 M, log2 N, log2 K), L1 distance, ties to the lower entry.  With no
  * manifest loaded, or when the picked variant cannot run the arguments
  * (alignment, transpose support), the next members of kappa are tried in
@@ -169,7 +174,9 @@ int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids,
  * t_best(s) / min_{v in kappa} t(v, s), t_best over every
  * valid variant of the table.  Writes the ids to out_ids[0..k) (-1 padded),
  * the training geomean to *out_train_geomean, and, when manifest_path is not
- * NULL, a manifest (kappa + each training shape's fastest member).  `seed`
+ * NULL, a manifest (kappa, each training shape's fastest member, the tree
+ * of PT_SELECT_TREE, and each member's time model when every training shape
+ * has the same transpose pair).  `seed`
  * drives the random restarts / initialisation of the heuristic methods.
  * CPU only. */
 int pt_select(const char *table_path, const int *train_idx, int n_train, int k,

@@ -152,6 +152,62 @@ def nearest_shape(query, shapes) -> int:
     return best
 
 
+# ---- time model for shapes outside the table ------------------------------------------
+#
+# The paper leaves inference for unlisted inputs open (Section V-G).  The
+# reading taken here: for every member of kappa, ln(time) is modelled as a
+# quadratic in the centred log-extents u = (log2 M - 9) / 3, v = (log2 N -
+# 9) / 3, w = (log2 K - 9) / 3, fitted by least squares on the training
+# shapes where the member is valid; the selector takes the member with the
+# smallest predicted time (ties to the earlier member).  With too few
+# training points for the quadratic (fewer than 10, or dependent columns)
+# the linear model in (1, u, v, w) is used, with fewer than that the mean.
+
+MODEL_FEATURES = 10
+
+
+def model_features(shape) -> list:
+    """[1, u, v, w, u^2, v^2, w^2, uv, uw, vw] of shape (M, N, K)."""
+    u, v, w = ((math.log2(x) - 9.0) / 3.0 for x in shape[:3])
+    return [1.0, u, v, w, u * u, v * v, w * w, u * v, u * w, v * w]
+
+
+def _full_rank(X) -> bool:
+    # Same criterion as the library's QR: every |R_ii| above 1e-9 of the largest.
+    r = np.abs(np.diag(np.linalg.qr(X, mode="r")))
+    return bool(len(r) == X.shape[1] and np.all(r > 1e-9 * r.max()))
+
+
+def model_fit(times_row, train_shapes):
+    """Coefficients (length 10) of one variant's ln-time model over the
+    training shapes, or None when the variant is valid on none of them."""
+    pts = [(model_features(sh), math.log(t)) for sh, t in zip(train_shapes, times_row)
+           if np.isfinite(t) and t > 0]
+    if not pts:
+        return None
+    X = np.array([f for f, _ in pts])
+    y = np.array([v for _, v in pts])
+    for p in (MODEL_FEATURES, 4):
+        if len(pts) >= p and _full_rank(X[:, :p]):
+            c = np.linalg.lstsq(X[:, :p], y, rcond=None)[0]
+            return [float(x) for x in c] + [0.0] * (MODEL_FEATURES - p)
+    return [float(np.mean(y))] + [0.0] * (MODEL_FEATURES - 1)
+
+
+def model_pick(coefs, query):
+    """Index of the member with the smallest predicted ln-time at `query`
+    (ties to the earlier member); None when no member has a model."""
+    f = np.array(model_features(query))
+    best, bp = None, None
+    for i, c in enumerate(coefs):
+        if c is None:
+            continue
+        pred = float(np.dot(np.array(c), f))
+        if bp is None or pred < bp:
+            best, bp = i, pred
+    return best
+
+
 # ---- alternative selections (Section IV-C) ---------------------------------------------
 #
 # Both work on the training shapes' performance vectors: shape s is the point

@@ -52,11 +52,23 @@ struct ManifestNode {
     int variant = -1;
 };
 
+// Time model of the runtime selector: per kappa member, ln(median ms) as a
+// quadratic in u = (log2 M - 9) / 3, v = (log2 N - 9) / 3, w = (log2 K - 9) / 3
+// with features [1, u, v, w, u^2, v^2, w^2, uv, uw, vw], least-squares fitted
+// on the training shapes (fewer terms when the member has too few valid
+// training shapes, none when it has none).
+constexpr int kModelFeatures = 10;
+void model_features(const pt_shape_t &s, double f[kModelFeatures]);
+
 struct Manifest {
     std::string method;
     std::vector<int> kappa;  // registry ids, in manifest order
     std::vector<ManifestEntry> map;
     std::vector<ManifestNode> tree;  // optional; shapes outside the map descend it
+    // Optional time model: coef[i] for kappa[i] (empty: no model for it);
+    // applies to shapes with transposes (model_ta, model_tb).
+    std::vector<std::vector<double>> coef;
+    char model_ta = 0, model_tb = 0;
     double train_geomean = 0;
 };
 

@@ -577,6 +577,83 @@ void select_tree(const Table &t, const std::vector<int> &shapes, const Problem &
 
 }  // namespace
 
+// ---- time model of the runtime selector -----------------------------------------------
+void model_features(const pt_shape_t &s, double f[kModelFeatures]) {
+    const double u = (std::log2((double)s.m) - 9.0) / 3.0, v = (std::log2((double)s.n) - 9.0) / 3.0,
+                 w = (std::log2((double)s.k) - 9.0) / 3.0;
+    const double x[kModelFeatures] = {1.0, u, v, w, u * u, v * v, w * w, u * v, u * w, v * w};
+    for (int i = 0; i < kModelFeatures; ++i) f[i] = x[i];
+}
+
+// Least squares min |X c - y| over the first p columns of X (n rows) by
+// Householder QR; false when the columns are numerically dependent
+// (|R_ii| <= 1e-9 max_j |R_jj|).
+static bool lstsq_qr(std::vector<std::vector<double>> X, std::vector<double> y, int p, std::vector<double> *c) {
+    const int n = (int)X.size();
+    if (n < p) return false;
+    std::vector<double> diag(p);
+    for (int j = 0; j < p; ++j) {
+        double norm = 0;
+        for (int i = j; i < n; ++i) norm += X[i][j] * X[i][j];
+        norm = std::sqrt(norm);
+        if (norm == 0) return false;
+        const double alpha = X[j][j] > 0 ? -norm : norm;
+        std::vector<double> vv(n, 0.0);
+        vv[j] = X[j][j] - alpha;
+        for (int i = j + 1; i < n; ++i) vv[i] = X[i][j];
+        double vn = 0;
+        for (int i = j; i < n; ++i) vn += vv[i] * vv[i];
+        if (vn > 0) {
+            for (int col = j; col < p; ++col) {
+                double d = 0;
+                for (int i = j; i < n; ++i) d += vv[i] * X[i][col];
+                d = 2 * d / vn;
+                for (int i = j; i < n; ++i) X[i][col] -= d * vv[i];
+            }
+            double d = 0;
+            for (int i = j; i < n; ++i) d += vv[i] * y[i];
+            d = 2 * d / vn;
+            for (int i = j; i < n; ++i) y[i] -= d * vv[i];
+        }
+        diag[j] = X[j][j];
+    }
+    double mx = 0;
+    for (int j = 0; j < p; ++j) mx = std::max(mx, std::fabs(diag[j]));
+    for (int j = 0; j < p; ++j)
+        if (std::fabs(diag[j]) <= 1e-9 * mx) return false;
+    c->assign(kModelFeatures, 0.0);
+    for (int j = p - 1; j >= 0; --j) {
+        double sacc = y[j];
+        for (int col = j + 1; col < p; ++col) sacc -= X[j][col] * (*c)[col];
+        (*c)[j] = sacc / X[j][j];
+    }
+    return true;
+}
+
+// Coefficients for one member from its valid training times: the quadratic
+// model when it is determined (>= 10 points, independent features), else the
+// linear one (>= 4), else the mean; empty when no training time is valid.
+static std::vector<double> fit_member(const std::vector<pt_shape_t> &shapes, const std::vector<double> &times) {
+    std::vector<std::vector<double>> X;
+    std::vector<double> y;
+    for (size_t j = 0; j < shapes.size(); ++j) {
+        if (!std::isfinite(times[j]) || times[j] <= 0) continue;
+        std::vector<double> f(kModelFeatures);
+        model_features(shapes[j], f.data());
+        X.push_back(f);
+        y.push_back(std::log(times[j]));
+    }
+    std::vector<double> c;
+    if (X.empty()) return c;
+    for (int p : {kModelFeatures, 4})
+        if ((int)X.size() >= p && lstsq_qr(X, y, p, &c)) return c;
+    c.assign(kModelFeatures, 0.0);
+    double sum = 0;
+    for (double v : y) sum += v;
+    c[0] = sum / (double)y.size();
+    return c;
+}
+
 // ---- manifest --------------------------------------------------------------------
 static std::string shape_json(const pt_shape_t &s) {
     char buf[160];
@@ -586,8 +663,8 @@ static std::string shape_json(const pt_shape_t &s) {
 }
 
 static int write_manifest(const char *path, const char *method, int k, double g, const std::vector<int> &kappa_ids,
-                          const std::vector<std::pair<pt_shape_t, int>> &map,
-                          const std::vector<TreeNode> *tree = nullptr) {
+                          const std::vector<std::pair<pt_shape_t, int>> &map, const std::vector<TreeNode> *tree,
+                          const std::vector<std::vector<double>> *coef, char ta, char tb) {
     std::ofstream o(path);
     if (!o) return set_error(PT_EIO, 9, "cannot write manifest '%s'", path);
     auto name = [](int id) {
@@ -618,6 +695,26 @@ static int write_manifest(const char *path, const char *method, int k, double g,
                                                            : "{\"variant\": " + json::quote(name(nd.variant)) + "}");
         }
         o << "\n  ]";
+    }
+    if (coef && !coef->empty()) {
+        // Time model (see model_features), one coefficient list per kappa member.
+        o << ",\n  \"model\": {\"transA\": \"" << ta << "\", \"transB\": \"" << tb
+          << "\", \"features\": \"1,u,v,w,u2,v2,w2,uv,uw,vw; u = (log2 M - 9) / 3\", \"coef\": [";
+        for (size_t i = 0; i < coef->size(); ++i) {
+            o << (i ? ",\n" : "\n") << "    ";
+            if ((*coef)[i].empty()) {
+                o << "null";
+                continue;
+            }
+            o << "[";
+            for (int f = 0; f < kModelFeatures; ++f) {
+                char buf[40];
+                std::snprintf(buf, sizeof(buf), "%.17g", (*coef)[i][f]);
+                o << (f ? ", " : "") << buf;
+            }
+            o << "]";
+        }
+        o << "\n  ]}";
     }
     o << "\n}\n";
     o.flush();
@@ -703,13 +800,39 @@ int read_manifest(const char *path, Manifest *out) {
             if (m.tree[i].feature >= 0 && (m.tree[i].left <= i || m.tree[i].right <= i))
                 return set_error(PT_EFORMAT, 1, "manifest: tree nodes out of order");
     }
+    if (const json::Value *md = root.get("model"); md) {
+        const json::Value *ta = md->get("transA"), *tb = md->get("transB"), *cf = md->get("coef");
+        if (!ta || !tb || !cf || ta->kind != json::Value::String || tb->kind != json::Value::String ||
+            ta->str.size() != 1 || tb->str.size() != 1 || cf->kind != json::Value::Array ||
+            cf->arr.size() != m.kappa.size())
+            return set_error(PT_EFORMAT, 1, "manifest: malformed model");
+        m.model_ta = ta->str[0];
+        m.model_tb = tb->str[0];
+        for (const auto &e : cf->arr) {
+            std::vector<double> c;
+            if (e.kind == json::Value::Array) {
+                if (e.arr.size() != (size_t)kModelFeatures) return set_error(PT_EFORMAT, 1, "manifest: bad model row");
+                for (const auto &x : e.arr) {
+                    if (x.kind != json::Value::Number || !std::isfinite(x.num))
+                        return set_error(PT_EFORMAT, 1, "manifest: bad model coefficient");
+                    c.push_back(x.num);
+                }
+            } else if (e.kind != json::Value::Null) {
+                return set_error(PT_EFORMAT, 1, "manifest: bad model row");
+            }
+            m.coef.push_back(std::move(c));
+        }
+    }
     *out = std::move(m);
     return PT_OK;
 }
 
-// Runtime selector (Fig. 1 inference step): exact hit, else nearest listed
-// shape with the same transposes (any transposes if none) in log2 space, L1
-// distance, ties to the earlier entry; with no map, the first member.
+// Runtime selector (Fig. 1 inference step): exact hit; else the tree (tree
+// manifests); else the time model (the member with the smallest predicted
+// time, ties to the earlier member; shapes with the model's transposes);
+// else the nearest listed shape with the same transposes (any transposes if
+// none) in log2 space, L1 distance, ties to the earlier entry; with no map,
+// the first member.
 int manifest_pick(const Manifest &m, const pt_shape_t &s) {
     if (m.kappa.empty()) return -1;
     if (m.map.empty()) return m.kappa[0];
@@ -721,6 +844,22 @@ int manifest_pick(const Manifest &m, const pt_shape_t &s) {
         for (size_t steps = 0; steps <= m.tree.size() && m.tree[node].feature >= 0; ++steps)
             node = f[m.tree[node].feature] <= m.tree[node].threshold ? m.tree[node].left : m.tree[node].right;
         if (m.tree[node].variant >= 0) return m.tree[node].variant;
+    }
+    if (!m.coef.empty() && s.transA == m.model_ta && s.transB == m.model_tb) {
+        double f[kModelFeatures];
+        model_features(s, f);
+        int best = -1;
+        double bp = kInf;
+        for (size_t i = 0; i < m.kappa.size() && i < m.coef.size(); ++i) {
+            if (m.coef[i].empty()) continue;
+            double pred = 0;
+            for (int j = 0; j < kModelFeatures; ++j) pred += m.coef[i][j] * f[j];
+            if (pred < bp) {
+                bp = pred;
+                best = m.kappa[i];
+            }
+        }
+        if (best >= 0) return best;
     }
     bool any_same_trans = false;
     for (const auto &e : m.map)
@@ -849,7 +988,23 @@ int pt_select(const char *table_path, const int *train_idx, int n_train, int k, 
             }
             if (best >= 0) map.emplace_back(t.shapes[shapes[j]], best);
         }
-        rc = write_manifest(manifest_path, mname, k, val, ids, map, method == PT_SELECT_TREE ? &tree : nullptr);
+        // Time model over the training shapes, when they share one transpose pair.
+        std::vector<std::vector<double>> coef;
+        bool one_pair = true;
+        for (int j = 1; j < p.S; ++j)
+            one_pair = one_pair && t.shapes[shapes[j]].transA == t.shapes[shapes[0]].transA &&
+                       t.shapes[shapes[j]].transB == t.shapes[shapes[0]].transB;
+        if (one_pair) {
+            std::vector<pt_shape_t> tr;
+            for (int j = 0; j < p.S; ++j) tr.push_back(t.shapes[shapes[j]]);
+            for (int c : set) {
+                std::vector<double> tv;
+                for (int j = 0; j < p.S; ++j) tv.push_back(t.t[p.cand[c]][shapes[j]]);
+                coef.push_back(fit_member(tr, tv));
+            }
+        }
+        rc = write_manifest(manifest_path, mname, k, val, ids, map, method == PT_SELECT_TREE ? &tree : nullptr,
+                            one_pair ? &coef : nullptr, t.shapes[shapes[0]].transA, t.shapes[shapes[0]].transB);
         if (rc != PT_OK) return rc;
     }
     return PT_OK;

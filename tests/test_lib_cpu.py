@@ -190,15 +190,15 @@ def test_score_best_of_set_and_selector(tmp_path):
     ids, val = pt.select(path, train, 3, method=pt.PT_SELECT_EXACT, manifest=man)
     # best-of-set scoring == Eq. 1 on the held-out shapes
     assert pt.score(path, held, ids) == pytest.approx(osel.set_performance(t, ids, held), rel=1e-12)
-    # selector-realised: each held-out shape takes its nearest training shape's pick
+    # selector-realised: each held-out shape takes the member with the smallest
+    # time predicted by the manifest's model (fitted on the training shapes)
     m = json.load(open(man))
     assert [e["variant"] for e in m["map"]] == [names[osel.best_in_set(t, ids, s)] for s in train]
     tb = osel.per_shape_best(t)
     logs = []
-    map_shapes = [shapes[s] for s in train]
+    coefs = [osel.model_fit(t[v, train], [shapes[s] for s in train]) for v in ids]
     for s in held:
-        j = osel.nearest_shape(shapes[s][:3], [x[:3] for x in map_shapes])
-        v = osel.best_in_set(t, ids, train[j])
+        v = ids[osel.model_pick(coefs, shapes[s][:3])]
         tv = t[v, s]
         if not np.isfinite(tv):
             fall = [t[i, s] for i in ids if np.isfinite(t[i, s])]
@@ -330,3 +330,58 @@ def test_kernel_timer_without_launches():
     assert pt.kernel_timer_stop() == (0.0, 0)
     # Stopping a timer that is not running is harmless too.
     assert pt.kernel_timer_stop() == (0.0, 0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_time_model_matches_oracle(seed, tmp_path):
+    # Tables on a 4 x 4 x 4 grid of shapes; the manifest's model coefficients
+    # equal the oracle's fit, and unlisted shapes get the oracle's pick.
+    levels = (128, 512, 1024, 4096)
+    shapes = [(m, n, k, "N", "N") for m in levels for n in levels for k in levels]
+    t = random_table(100 + seed, 10, len(shapes), invalid=0.15)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t, shapes=shapes)
+    rng = np.random.default_rng(seed)
+    train = sorted(rng.choice(len(shapes), 32, replace=False).tolist())
+    man = str(tmp_path / "m.json")
+    ids, _ = pt.select(path, train, 4, manifest=man)
+    ids = [i for i in ids if i >= 0]
+    m = json.load(open(man))
+    coefs = [osel.model_fit(t[v, train], [shapes[s][:3] for s in train]) for v in ids]
+    for got, want in zip(m["model"]["coef"], coefs):
+        if want is None:
+            assert got is None
+        else:
+            assert np.allclose(got, want, rtol=1e-8, atol=1e-8)
+    pt.load_manifest(man)
+    try:
+        # extents divisible by 16, so that every variant's alignment rules admit them
+        for q in [(208, 704, 3008), (128, 4096, 304), (3008, 160, 160), (784, 784, 784), (112, 112, 5008)]:
+            f = np.array(osel.model_features(q))
+            preds = sorted(float(np.dot(c, f)) for c in coefs if c is not None)
+            if len(preds) > 1 and preds[1] - preds[0] < 1e-9:
+                continue  # a near tie: either member is a correct pick
+            assert pt.selected_variant(*q) == ids[osel.model_pick(coefs, q)]
+        # listed shapes keep their fastest member
+        s = train[5]
+        assert pt.selected_variant(*shapes[s][:3]) == osel.best_in_set(t, ids, s)
+    finally:
+        pt.load_manifest(None)
+
+
+def test_manifest_without_model_uses_nearest_shape(tmp_path):
+    # Training shapes with mixed transposes get no model: the nearest listed shape decides.
+    shapes = [(128, 128, 128, "N", "N"), (4096, 4096, 4096, "N", "N"), (128, 128, 128, "N", "T"),
+              (4096, 4096, 4096, "N", "T")]
+    t = np.array([[1.0, 9.0, 1.0, 9.0], [9.0, 1.0, 9.0, 1.0], [5.0, 5.0, 5.0, 5.0]])
+    path = str(tmp_path / "t.csv")
+    write_table(path, t, shapes=shapes)
+    man = str(tmp_path / "m.json")
+    ids, _ = pt.select(path, [0, 1, 2, 3], 2, manifest=man)
+    assert "model" not in json.load(open(man))
+    pt.load_manifest(man)
+    try:
+        assert pt.selected_variant(200, 200, 200) == 0
+        assert pt.selected_variant(3000, 3000, 3000, transB="T") == 1
+    finally:
+        pt.load_manifest(None)

@@ -220,3 +220,54 @@ def test_tree_first_split_maximises_error_reduction_by_brute_force():
                 best = gain if best is None else max(best, gain)
     got = sse(list(range(10))) - sse(leaves[0][0]) - sse(leaves[1][0])
     assert got == pytest.approx(best, rel=1e-9)
+
+
+# ---- time model of the runtime selector (the reading for shapes outside the table) ----
+
+def _grid(levels=(128, 512, 1024, 4096)):
+    return [(m, n, k) for m in levels for n in levels for k in levels]
+
+
+def test_model_recovers_a_planted_quadratic():
+    rng = np.random.default_rng(11)
+    shapes = _grid()
+    beta = rng.normal(0, 1, osel.MODEL_FEATURES)
+    times = [math.exp(float(np.dot(beta, osel.model_features(s)))) for s in shapes]
+    c = osel.model_fit(times, shapes)
+    assert np.allclose(c, beta, rtol=0, atol=1e-9)
+
+
+def test_model_degrades_to_linear_then_mean():
+    rng = np.random.default_rng(12)
+    shapes = [(128, 512, 1024), (4096, 512, 128), (512, 4096, 512), (1024, 128, 4096), (256, 256, 256)]
+    beta = np.concatenate([rng.normal(0, 1, 4), np.zeros(6)])
+    times = [math.exp(float(np.dot(beta, osel.model_features(s)))) for s in shapes]
+    c = osel.model_fit(times, shapes)            # 5 points: the quadratic is not determined
+    assert np.allclose(c, beta, atol=1e-9)
+    c2 = osel.model_fit([2.0, 8.0, math.inf], shapes[:3])   # 2 valid points: the mean of ln t
+    assert c2[0] == pytest.approx(math.log(4.0)) and not any(c2[1:])
+    assert osel.model_fit([math.inf] * 3, shapes[:3]) is None
+    # dependent columns (every shape has the same N): no linear model either, the mean
+    same_n = [(m, 512, k) for m in (128, 512, 1024, 4096) for k in (128, 512, 1024)]
+    c3 = osel.model_fit([float(i + 1) for i in range(len(same_n))], same_n)
+    assert c3[0] == pytest.approx(float(np.mean(np.log(np.arange(1, 13))))) and not any(c3[1:])
+
+
+def test_model_pick_is_the_argmin_of_the_models():
+    rng = np.random.default_rng(13)
+    coefs = [list(rng.normal(0, 1, osel.MODEL_FEATURES)) for _ in range(5)]
+    coefs[2] = None
+    for q in [(300, 700, 2000), (128, 4096, 128), (5000, 100, 900)]:
+        f = np.array(osel.model_features(q))
+        preds = [np.dot(c, f) if c is not None else np.inf for c in coefs]
+        assert osel.model_pick(coefs, q) == int(np.argmin(preds))
+    # ties go to the earlier member; no model at all gives None
+    same = [1.0] + [0.0] * 9
+    assert osel.model_pick([same, same], (512, 512, 512)) == 0
+    assert osel.model_pick([None, None], (512, 512, 512)) is None
+
+
+def test_model_features_closed_form():
+    # log2 512 = 9 is the centre; 4096 and 64 sit one scale unit (3 octaves) away.
+    assert osel.model_features((512, 512, 512)) == [1.0] + [0.0] * 9
+    assert osel.model_features((4096, 64, 512)) == [1.0, 1.0, -1.0, 0.0, 1.0, 1.0, 0.0, -1.0, 0.0, 0.0]
