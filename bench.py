@@ -583,6 +583,53 @@ def traffic_for(kernel, shape):
 
 
 # ---- CPU oracle baseline -----------------------------------------------------------------
+def per_shape_times(calls, stream, reps=3):
+    """Median device time of each call in `calls` (issued in order on `stream`).
+
+    The calls are captured once in a CUDA graph with a timing event recorded
+    between consecutive calls, and the graph is replayed `reps` times, so host
+    launch latency never sits between two events.  The event nodes also
+    separate the calls, so no call overlaps its neighbour.  Where a timing
+    event cannot be captured, the calls are issued eagerly between events
+    instead.  Returns (per-call ms, method)."""
+    import torch
+
+    n = len(calls)
+    times = [[] for _ in range(n)]
+    try:
+        ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n + 1)]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(g, stream=stream):
+                ev[0].record(stream)
+                for i, c in enumerate(calls):
+                    c()
+                    ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        for _ in range(reps):
+            g.replay()
+            torch.cuda.synchronize()
+            for i in range(n):
+                times[i].append(ev[i].elapsed_time(ev[i + 1]))
+        del g
+        method = "graph replay, timing events between calls"
+    except (RuntimeError, TypeError):
+        torch.cuda.synchronize()
+        times = [[] for _ in range(n)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                ev[0].record(stream)
+                for i, c in enumerate(calls):
+                    c()
+                    ev[i + 1].record(stream)
+                stream.synchronize()
+                for i in range(n):
+                    times[i].append(ev[i].elapsed_time(ev[i + 1]))
+        method = "eager, timing events between calls (includes host launch gaps)"
+    return [statistics.median(x) for x in times], method
+
+
 def cpu_oracle_sample(shapes, rows_per_shape, seed_base=1000):
     """Times the FP64 CPU oracle on the first `rows_per_shape` rows of every
     shape (all rows when M is smaller).  Returns (TFLOP/s, seconds, cores, flops)."""
@@ -759,19 +806,9 @@ def main():
             step()
     torch.cuda.synchronize()
 
-    # ---- per-shape times (events around each launch, same order) ----
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(shapes) + 1)]
-    per_shape = [[] for _ in shapes]
-    with torch.cuda.stream(stream):
-        for rep in range(3):
-            ev[0].record(stream)
-            for i in range(len(shapes)):
-                pt.sgemm(devA[i], devB[i], devC[i], stream=stream)
-                ev[i + 1].record(stream)
-            stream.synchronize()
-            for i in range(len(shapes)):
-                per_shape[i].append(ev[i].elapsed_time(ev[i + 1]))
-    shape_ms = [statistics.median(x) for x in per_shape]
+    # ---- per-shape times: timing events between the calls of a captured graph ----
+    shape_ms, per_shape_timing = per_shape_times(
+        [lambda i=i: pt.sgemm(devA[i], devB[i], devC[i], stream=stream) for i in range(len(shapes))], stream)
 
     # ---- timed region: graph replays ----
     try:
@@ -938,20 +975,12 @@ def main():
     # cuBLAS SGEMM (FP32, TF32 off) on the same shapes, as context.
     torch.backends.cuda.matmul.allow_tf32 = False
     torch.set_float32_matmul_precision("highest")
-    cub_ms = [[] for _ in shapes]
     with torch.cuda.stream(stream):
         for i in range(len(shapes)):
             torch.matmul(devA[i], devB[i], out=devC[i])
         stream.synchronize()
-        for _ in range(3):
-            ev[0].record(stream)
-            for i in range(len(shapes)):
-                torch.matmul(devA[i], devB[i], out=devC[i])
-                ev[i + 1].record(stream)
-            stream.synchronize()
-            for i in range(len(shapes)):
-                cub_ms[i].append(ev[i].elapsed_time(ev[i + 1]))
-    cub_ms = [statistics.median(x) for x in cub_ms]
+    cub_ms, _ = per_shape_times(
+        [lambda i=i: torch.matmul(devA[i], devB[i], out=devC[i]) for i in range(len(shapes))], stream)
     cublas_tflops = step_flops / (sum(cub_ms) * 1e-3) / 1e12
 
     cpu = None
@@ -995,7 +1024,7 @@ def main():
                        "gbs": round(4.0 * (s[0] * s[2] + s[2] * s[1] + s[0] * s[1]) / (ms * 1e-3) / 1e9, 1),
                        "variant": pt.variant(p)["name"], "cublas_tflops": round(f / (cm * 1e-3) / 1e12, 3)}
                       for s, ms, f, p, cm in zip(shapes, shape_ms, flops, picks, cub_ms)],
-        "context": {"cublas_sgemm_tflops": cublas_tflops, "cublas_math": "FP32 (allow_tf32=False, precision highest)",
+        "context": {"per_shape_timing": per_shape_timing, "cublas_sgemm_tflops": cublas_tflops, "cublas_math": "FP32 (allow_tf32=False, precision highest)",
                     "per_shape_wins_vs_cublas": sum(1 for m, c in zip(shape_ms, cub_ms) if m <= c),
                     "sum_ms_ours": sum(shape_ms), "sum_ms_cublas": sum(cub_ms),
                     "fp32_peak_tflops_at_max_clock": peak, "sms": sms},
