@@ -275,6 +275,25 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcBf16x3, 64, 3, 2, 64, 0, 2>>("tcbf16x3_m128n64_p3_sw64_fa_sk2"),
         tc_entry<Tc<kTcBf16x3, 64, 3, 4, 64, 0, 2>>("tcbf16x3_m128n64_p3_sw64_fa_sk4"),
         tc_entry<Tc<kTcBf16x3, 64, 3, 1, 64, 1, 2>>("tcbf16x3_m128n64_p3_sw64_fa_stk"),
+        // Deeper fused pipelines (64-byte rows): more FP32 bytes in flight per SM
+        // for the skinny, long-K shapes whose loads are latency-bound.
+        tc_entry<Tc<kTcBf16x3, 64, 4, 1, 64, 0, 2>>("tcbf16x3_m128n64_p4_sw64_fa"),
+        tc_entry<Tc<kTcBf16x3, 64, 4, 2, 64, 0, 2>>("tcbf16x3_m128n64_p4_sw64_fa_sk2"),
+        tc_entry<Tc<kTcBf16x3, 64, 4, 4, 64, 0, 2>>("tcbf16x3_m128n64_p4_sw64_fa_sk4"),
+        tc_entry<Tc<kTcBf16x3, 64, 5, 1, 64, 0, 1>>("tcbf16x3_m128n64_p5_sw64_fb"),
+        tc_entry<Tc<kTcBf16x3, 64, 5, 2, 64, 0, 1>>("tcbf16x3_m128n64_p5_sw64_fb_sk2"),
+        tc_entry<Tc<kTcBf16x3, 64, 5, 4, 64, 0, 1>>("tcbf16x3_m128n64_p5_sw64_fb_sk4"),
+        // Fused 128-column tiles: with N (fused A) or M (fused B) at most 128
+        // each FP32 element is converted once, and the tensor core reads the
+        // other operand's planes once per 128 columns instead of per 64.
+        tc_entry<Tc<kTcBf16x3, 128, 3, 1, 64, 0, 2>>("tcbf16x3_m128n128_p3_sw64_fa"),
+        tc_entry<Tc<kTcBf16x3, 128, 3, 2, 64, 0, 2>>("tcbf16x3_m128n128_p3_sw64_fa_sk2"),
+        tc_entry<Tc<kTcBf16x3, 128, 3, 4, 64, 0, 2>>("tcbf16x3_m128n128_p3_sw64_fa_sk4"),
+        tc_entry<Tc<kTcBf16x3, 128, 3, 1, 64, 1, 2>>("tcbf16x3_m128n128_p3_sw64_fa_stk"),
+        tc_entry<Tc<kTcBf16x3, 128, 3, 1, 64, 0, 1>>("tcbf16x3_m128n128_p3_sw64_fb"),
+        tc_entry<Tc<kTcBf16x3, 128, 3, 2, 64, 0, 1>>("tcbf16x3_m128n128_p3_sw64_fb_sk2"),
+        tc_entry<Tc<kTcBf16x3, 128, 3, 4, 64, 0, 1>>("tcbf16x3_m128n128_p3_sw64_fb_sk4"),
+        tc_entry<Tc<kTcBf16x3, 128, 3, 1, 64, 1, 1>>("tcbf16x3_m128n128_p3_sw64_fb_stk"),
         // BF16x3 64-column tiles with room for the coalescing epilogue stage.
         tc_entry<Tc<kTcBf16x3, 64, 2>>("tcbf16x3_m128n64_p2"),
         tc_entry<Tc<kTcBf16x3, 64, 2, 4>>("tcbf16x3_m128n64_p2_sk4"),

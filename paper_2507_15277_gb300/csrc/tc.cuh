@@ -120,6 +120,14 @@ struct Tc {
     // 256-thread CTA.
     static constexpr int CONV_WARP0 = EPI_WARPS + 2, CONV_WARPS = FUSE ? (BN >= 128 ? 2 : 4) : 0;
     static constexpr int THREADS = 32 * (EPI_WARPS + 2 + CONV_WARPS);
+    // Fused versions: the epilogue warps convert too.  They drain the
+    // accumulator only once per 128 values of k, so between drains they take
+    // an equal share of every stage's conversion next to the converter warps.
+    // Not in 64-column stream-K versions: with the stream-K epilogue the
+    // conversion code no longer fits the registers of a 320-thread CTA.
+    static constexpr bool EPI_CONV = FUSE != 0 && !(STREAMK != 0 && BN == 64);
+    static constexpr int CONV_ALL_WARPS = FUSE ? (EPI_CONV ? EPI_WARPS : 0) + CONV_WARPS : 0;
+    static constexpr int CONV_THREADS = 32 * CONV_ALL_WARPS;
     // Epilogue staging (when it fits): each epilogue warp transposes its 32
     // rows through a 32 x STG_LD float buffer, 32 columns at a time, so that
     // C is written in whole 128-byte row segments.
@@ -245,6 +253,79 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Fused split: converting thread ct (0 <= ct < V::CONV_THREADS) writes its
+// share of the stage's three BF16 planes of the fused operand from the FP32
+// tile the producer loaded, K-major in the swizzled layout a TMA load would
+// produce (16-byte chunk c of plane row r at chunk c ^ ((r * SWZ / 128) &
+// (SWZ / 16 - 1))).  x = b0 + b1 + b2 with b0 = RN_bf16(x), b1 = RN_bf16(x - b0),
+// b2 = RN_bf16(x - b0 - b1); both subtractions are exact.
+template <class V>
+__device__ __forceinline__ void tc_convert_stage(unsigned char *stp, int ct) {
+    constexpr int BK = V::BK, BN = V::BN, P = V::P, KC = BK / 8, NCT = V::CONV_THREADS;
+    const float *bf = reinterpret_cast<const float *>(stp + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES));
+    unsigned char *bp = stp + (V::FUSEB ? P * V::A_PLANE_BYTES : 0);
+    if constexpr (V::FUSEB) {
+        // B: lanes take consecutive n of one k chunk (the FP32 tile is
+        // [k][n]) and each writes one 16-byte chunk of every plane.
+#pragma unroll 2
+        for (int it = ct; it < BN * KC; it += NCT) {
+            const int n = it % BN, kc = it / BN;
+            float x[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = bf[(kc * 8 + e) * BN + n];
+            uint32_t b[3][4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                float v0 = x[e], v1 = x[e + 1];
+#pragma unroll
+                for (int pl = 0; pl < 3; ++pl) {
+                    const uint32_t q = bf16x2_rn(v0, v1);
+                    b[pl][e / 2] = q;
+                    v0 -= bf16_lo_f32(q);
+                    v1 -= bf16_hi_f32(q);
+                }
+            }
+            const int sw = (n * V::SWZ / 128) & (V::SWZ / 16 - 1);
+            const int off = n * V::SWZ + ((kc ^ sw) << 4);
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl)
+                *reinterpret_cast<uint4 *>(bp + pl * V::B_PLANE_BYTES + off) =
+                    make_uint4(b[pl][0], b[pl][1], b[pl][2], b[pl][3]);
+        }
+    } else {
+        // A: consecutive lanes read consecutive 16-byte pieces of the [m][k]
+        // tile (no bank conflicts); a piece is four k values, half of one
+        // 16-byte plane chunk.
+        constexpr int HC = 2 * KC;  // pieces per row
+#pragma unroll 2
+        for (int it = ct; it < V::BM * HC; it += NCT) {
+            const int n = it / HC, h = it % HC;
+            const float4 x4 = *reinterpret_cast<const float4 *>(bf + n * BK + h * 4);
+            const float x[4] = {x4.x, x4.y, x4.z, x4.w};
+            uint32_t b[3][2];
+#pragma unroll
+            for (int e = 0; e < 4; e += 2) {
+                float v0 = x[e], v1 = x[e + 1];
+#pragma unroll
+                for (int pl = 0; pl < 3; ++pl) {
+                    const uint32_t q = bf16x2_rn(v0, v1);
+                    b[pl][e / 2] = q;
+                    v0 -= bf16_lo_f32(q);
+                    v1 -= bf16_hi_f32(q);
+                }
+            }
+            const int sw = (n * V::SWZ / 128) & (V::SWZ / 16 - 1);
+            const int off = n * V::SWZ + (((h >> 1) ^ sw) << 4) + ((h & 1) << 3);
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl)
+                *reinterpret_cast<uint2 *>(bp + pl * V::A_PLANE_BYTES + off) = make_uint2(b[pl][0], b[pl][1]);
+        }
+    }
+    // Generic-proxy writes become visible to the tensor core's (async-proxy)
+    // reads before the stage is handed over.
+    fence_proxy_async_smem();
+}
+
 // Tile coordinates of 1-D tile index t: consecutive indices walk GROUP_M
 // tile rows down before moving right (keeps a wave's panels in L2).
 template <class V>
@@ -317,7 +398,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
-            if (V::FUSE) mbar_init(conv0 + 8 * s, V::CONV_WARPS);
+            if (V::FUSE) mbar_init(conv0 + 8 * s, V::CONV_ALL_WARPS);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf0 + 8 * b, 1);
@@ -441,13 +522,10 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             s_consumed = g;
         }
     } else if (V::FUSE && warp >= V::CONV_WARP0) {
-        // Converter warps: split each stage's FP32 tile of the fused operand
-        // into the three BF16 planes, written K-major in the same swizzled
-        // layout a TMA load would produce (16-byte chunk c of plane row r at
-        // chunk c ^ ((r * SWZ / 128) & (SWZ / 16 - 1))).
+        // Converter warps: their share of every stage's conversion (the
+        // epilogue warps take the rest).
         if constexpr (V::FUSE) {
-            const int ct = tid - 32 * V::CONV_WARP0;  // 0 .. 32 * CONV_WARPS - 1
-            constexpr int KC = BK / 8;                // 16-byte chunks per plane row
+            const int ct = (V::EPI_CONV ? 32 * V::EPI_WARPS : 0) + (tid - 32 * V::CONV_WARP0);
             int g = 0;
             bool ok = true;
             for (int i = 0; ok && i < nseg; ++i) {
@@ -462,49 +540,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         ok = false;
                         break;
                     }
-                    unsigned char *stp = smem_raw + (sbase - raw) + s * V::STAGE_BYTES;
-                    const float *bf = reinterpret_cast<const float *>(stp + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES));
-                    unsigned char *bp = stp + (V::FUSEB ? P * V::A_PLANE_BYTES : 0);
-                    constexpr int ROWS = V::FUSEB ? BN : V::BM;  // plane rows of the fused operand
-                    constexpr int PLANE = V::FUSEB ? V::B_PLANE_BYTES : V::A_PLANE_BYTES;
-#pragma unroll
-                    for (int it = ct; it < ROWS * KC; it += 32 * V::CONV_WARPS) {
-                        // B: lanes take consecutive n of one k chunk (the FP32
-                        // tile is [k][n]); A: KC lanes share a row, so a warp
-                        // reads whole rows of the [m][k] tile.
-                        const int n = V::FUSEB ? it % ROWS : it / KC, kc = V::FUSEB ? it / ROWS : it % KC;
-                        float x[8];
-                        if constexpr (V::FUSEB) {
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) x[e] = bf[(kc * 8 + e) * BN + n];
-                        } else {
-                            const float4 lo = *reinterpret_cast<const float4 *>(bf + n * BK + kc * 8);
-                            const float4 hi = *reinterpret_cast<const float4 *>(bf + n * BK + kc * 8 + 4);
-                            x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
-                            x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
-                        }
-                        uint32_t b[3][4];
-#pragma unroll
-                        for (int e = 0; e < 8; e += 2) {
-                            float v0 = x[e], v1 = x[e + 1];
-#pragma unroll
-                            for (int pl = 0; pl < 3; ++pl) {
-                                const uint32_t q = bf16x2_rn(v0, v1);
-                                b[pl][e / 2] = q;
-                                v0 -= bf16_lo_f32(q);
-                                v1 -= bf16_hi_f32(q);
-                            }
-                        }
-                        const int sw = (n * V::SWZ / 128) & (V::SWZ / 16 - 1);
-                        const int off = n * V::SWZ + ((kc ^ sw) << 4);
-#pragma unroll
-                        for (int pl = 0; pl < 3; ++pl)
-                            *reinterpret_cast<uint4 *>(bp + pl * PLANE + off) =
-                                make_uint4(b[pl][0], b[pl][1], b[pl][2], b[pl][3]);
-                    }
-                    // Generic-proxy writes become visible to the tensor core's
-                    // (async-proxy) reads before the stage is handed over.
-                    fence_proxy_async_smem();
+                    tc_convert_stage<V>(smem_raw + (sbase - raw) + s * V::STAGE_BYTES, ct);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(conv0 + 8 * s);
                 }
@@ -513,9 +549,14 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     } else {
         // Epilogue warps: drain each chunk's accumulator into FP32 registers,
         // then store the tile (SPLITK == 1) or keep it for the reduction.
+        // Fused versions (EPI_CONV): first convert this warp's share of chunk ch's
+        // stages, then drain chunk ch - 1, so the conversions the MMAs wait
+        // for never queue behind a drain; the drain only waits for MMAs of
+        // stages converted earlier.
         const int sub = warp & 3, grp = warp >> 2;
         const uint32_t lane_base = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(grp * COLS);
         int c = 0;  // chunks drained (all segments)
+        int g = 0;  // k-tiles converted (fused versions)
         unsigned epoch1 = 0;  // stream-K: this launch's flag value
         if constexpr (V::STREAMK != 0) epoch1 = ld_acquire_u32(args.sk_words) + 1u;
         for (int i = 0; epi_ok && i < nseg; ++i) {
@@ -523,7 +564,26 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             work.seg(i, t, c0, c1);
 #pragma unroll
             for (int j = 0; j < COLS; ++j) racc[j] = 0.f;
-            for (int ch = c0; ch < c1; ++ch, ++c) {
+            constexpr int DEFER = V::EPI_CONV ? 1 : 0;  // drains run one chunk behind the conversions
+            for (int ch = c0; ch < c1 + DEFER; ++ch) {
+                if constexpr (V::EPI_CONV) {
+                    const int kt_end = c1 * CKT < nkt ? c1 * CKT : nkt;
+                    const int k_hi = (ch + 1) * CKT < kt_end ? (ch + 1) * CKT : kt_end;
+                    for (int kt = ch * CKT; ch < c1 && kt < k_hi; ++kt, ++g) {
+                        const int s = g % STAGES, u = g / STAGES;
+                        const bool landed = mbar_wait_bounded(full0 + 8 * s, (uint32_t)(u & 1), kWaitLimitNs);
+                        if (!__all_sync(0xffffffffu, landed)) {
+                            s_fail = 1;
+                            epi_ok = false;
+                            break;
+                        }
+                        tc_convert_stage<V>(smem_raw + (sbase - raw) + s * V::STAGE_BYTES, tid);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(conv0 + 8 * s);
+                    }
+                    if (!epi_ok) break;
+                    if (ch == c0) continue;
+                }
                 const int b = c & 1;
                 const bool ok = mbar_wait_bounded(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -544,6 +604,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acce0 + 8 * b);
+                ++c;
             }
             if (V::STREAMK != 0 && epi_ok && c1 < nchunks) {
                 // Contributor: this CTA's partial tile goes to the workspace;

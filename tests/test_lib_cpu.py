@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_registry_rules():
     n = pt.num_variants()
-    assert 300 <= n <= 420
+    assert 300 <= n <= 448  # the GPU parity tests cover ids 0..447
     names = set()
     simt = []
     for i in range(n):
