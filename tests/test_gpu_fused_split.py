@@ -20,7 +20,12 @@ DEV = "cuda:0"
 PAIRS = [("tcbf16x3_m128n64_p2_fb", "tcbf16x3_m128n64_p2"),
          ("tcbf16x3_m128n64_p2_fb_sk2", "tcbf16x3_m128n64_p2"),
          ("tcbf16x3_m128n64_p2_fb_sk4", "tcbf16x3_m128n64_p2_sk4"),
-         ("tcbf16x3_m128n64_p2_fb_stk", "tcbf16x3_m128n64_p2")]
+         ("tcbf16x3_m128n64_p2_fb_stk", "tcbf16x3_m128n64_p2"),
+         # 64-byte rows: the twin with the same rows, tile and chunk order
+         ("tcbf16x3_m128n64_p5_sw64_fb", "tcbf16x3_m128n64_p4_sw64"),
+         ("tcbf16x3_m128n128_p3_sw64_fb", "tcbf16x3_m128n128_p4_sw64"),
+         ("tcbf16x3_m128n128_p3_sw64_fb_sk4", "tcbf16x3_m128n128_p4_sw64_sk4"),
+         ("tcbf16x3_m128n128_p3_sw64_fb_stk", "tcbf16x3_m128n128_p4_sw64")]
 SHAPES = [(128, 4096, 4096), (128, 1000, 1000), (300, 200, 520), (640, 320, 2176)]
 
 
@@ -77,7 +82,11 @@ def test_fused_b_declines_unreadable_b():
 PAIRS_A = [("tcbf16x3_m128n64_p3_sw64_fa", "tcbf16x3_m128n64_p4_sw64"),
            ("tcbf16x3_m128n64_p3_sw64_fa_sk2", "tcbf16x3_m128n64_p4_sw64"),
            ("tcbf16x3_m128n64_p3_sw64_fa_sk4", "tcbf16x3_m128n64_p4_sw64_sk4"),
-           ("tcbf16x3_m128n64_p3_sw64_fa_stk", "tcbf16x3_m128n64_p4_sw64")]
+           ("tcbf16x3_m128n64_p3_sw64_fa_stk", "tcbf16x3_m128n64_p4_sw64"),
+           ("tcbf16x3_m128n64_p4_sw64_fa", "tcbf16x3_m128n64_p4_sw64"),
+           ("tcbf16x3_m128n128_p3_sw64_fa", "tcbf16x3_m128n128_p4_sw64"),
+           ("tcbf16x3_m128n128_p3_sw64_fa_sk4", "tcbf16x3_m128n128_p4_sw64_sk4"),
+           ("tcbf16x3_m128n128_p3_sw64_fa_stk", "tcbf16x3_m128n128_p4_sw64")]
 SHAPES_A = [(4096, 128, 4096), (1000, 128, 1000), (300, 200, 520), (640, 320, 2176)]
 
 

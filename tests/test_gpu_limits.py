@@ -18,7 +18,8 @@ pt = pytest.importorskip("paper_2507_15277_gb300")
 
 DEV = "cuda:0"
 VARIANTS = [None, "s128x128x8_w32x64_t8x8_kl1_v1_p2_sk1_cpm", "tcbf16x3_m128n128_p4_sw64_stk",
-            "tcbf16x3_m128n64_p3_sk8", "tc3xtf32_m128n128_p3", "tcbf16x3_m128n64_p2_fb_sk4"]
+            "tcbf16x3_m128n64_p3_sk8", "tc3xtf32_m128n128_p3", "tcbf16x3_m128n64_p2_fb_sk4",
+            "tcbf16x3_m128n128_p3_sw64_fa_sk4", "tcbf16x3_m128n128_p3_sw64_fb_stk"]
 
 
 def _check(M, N, K, name, kind="uniform", rows=16):
