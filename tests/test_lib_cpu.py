@@ -385,3 +385,46 @@ def test_manifest_without_model_uses_nearest_shape(tmp_path):
         assert pt.selected_variant(3000, 3000, 3000, transB="T") == 1
     finally:
         pt.load_manifest(None)
+
+
+def test_malformed_time_model_is_rejected(tmp_path):
+    # Planted mistakes in the manifest's model block: each must fail to load
+    # with PT_EFORMAT; a block whose only change is a null row loads.
+    levels = (128, 512, 1024, 4096)
+    shapes = [(m, n, k, "N", "N") for m in levels for n in levels for k in levels]
+    t = random_table(7, 6, len(shapes), invalid=0.0)
+    path = str(tmp_path / "t.csv")
+    write_table(path, t, shapes=shapes)
+    man = str(tmp_path / "m.json")
+    ids, _ = pt.select(path, list(range(0, 64, 2)), 3, manifest=man)
+    good = json.load(open(man))
+    assert len(good["model"]["coef"]) == len(good["kappa"])
+
+    def mutated(fn):
+        m = json.loads(json.dumps(good))
+        fn(m["model"])
+        p = str(tmp_path / "bad.json")
+        with open(p, "w") as f:
+            f.write(json.dumps(m).replace("Infinity", "1e999"))
+        return p
+
+    bad = [
+        lambda md: md["coef"].pop(),                      # one row fewer than kappa
+        lambda md: md["coef"][0].pop(),                   # nine coefficients
+        lambda md: md["coef"][0].__setitem__(3, "x"),     # not a number
+        lambda md: md["coef"][0].__setitem__(0, float("inf")),  # not finite
+        lambda md: md.__setitem__("transA", "NN"),        # not one character
+        lambda md: md.pop("transB"),                      # missing field
+        lambda md: md["coef"].__setitem__(1, 3.0),        # row neither a list nor null
+    ]
+    for fn in bad:
+        with pytest.raises(pt.PtError) as e:
+            pt.load_manifest(mutated(fn))
+        assert e.value.code == _lib.PT_EFORMAT
+    # A member without a model (null row) is allowed.
+    ok = mutated(lambda md: md["coef"].__setitem__(0, None))
+    pt.load_manifest(ok)
+    try:
+        assert pt.selected_variant(208, 704, 3008) in ids
+    finally:
+        pt.load_manifest(None)
