@@ -2,6 +2,7 @@
 selector inside pt_sgemm."""
 
 import csv
+import json
 import os
 
 import numpy as np
@@ -109,9 +110,20 @@ def test_manifest_drives_pt_sgemm(small_table, tmp_path):
             torch.cuda.synchronize()
             ref = og.gemm(A.cpu().numpy(), B.cpu().numpy())
             assert normalised_error(C.cpu().numpy(), ref, K, 1.0, 1.0) <= TOL_FP32
-        # Unlisted shape: nearest listed shape's pick.
-        q = (130, 500, 1000)
-        idx = osel.nearest_shape(q, shapes)
-        assert pt.selected_variant(*q) == pt.selected_variant(*shapes[idx])
+        # Unlisted shape (extents divisible by 16, so every member admits it):
+        # the manifest's time model picks the member of least predicted time,
+        # or, without a model, the nearest listed shape's pick decides.
+        q = (144, 496, 1008)
+        m = json.load(open(man))
+        kappa = [pt.variant_by_name(n) for n in m["kappa"]]
+        coefs = m["model"]["coef"] if "model" in m else None
+        if coefs is not None:
+            f = np.array(osel.model_features(q))
+            preds = sorted(float(np.dot(c, f)) for c in coefs if c is not None)
+            if len(preds) < 2 or preds[1] - preds[0] > 1e-9:  # a near tie admits either member
+                assert pt.selected_variant(*q) == kappa[osel.model_pick(coefs, q)]
+        else:
+            idx = osel.nearest_shape(q, shapes)
+            assert pt.selected_variant(*q) == pt.selected_variant(*shapes[idx])
     finally:
         pt.load_manifest(None)
