@@ -22,6 +22,9 @@ CHAINS = [
     ["s128x128x8_w32x64_t8x8_kl1_v1_p2_sk1_cpm", "tcbf16x3_m128n128_p2", "tc3xtf32_m128n128_p3",
      "s128x128x8_w32x64_t8x8_kl1_v1_p2_sk1_cpm"],
     ["tcbf16x3_m128n128_p4_sw64", "tc3xtf32_m128n64_p4_sk4", "tcbf16x3_m128n64_p3", "tcbf16x3_m128n128_p2_sk2"],
+    # fused split and stream-K: a fused-A GEMM reads its predecessor's output itself
+    ["tcbf16x3_m128n128_p3_sw64_fa_sk4", "tcbf16x3_m128n128_p4_sw64_stk", "tcbf16x3_m128n128_p3_sw64_fb_stk",
+     "tcbf16x3_m128n64_p3_sw64_fa_stk"],
 ]
 
 
