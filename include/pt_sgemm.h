@@ -196,7 +196,22 @@ int pt_table_shapes(const char *table_path, int *out_n);
 int pt_table_shape(const char *table_path, int i, pt_shape_t *out);
 
 /* Installs the manifest used by pt_sgemm (process-wide, mutex-guarded);
- * NULL clears it. */
+ * NULL clears it.  PT_EIO when the file cannot be read, PT_EFORMAT when it
+ * is not a manifest of this form (one JSON object; pt_select writes it):
+ *   "format": "pt-manifest-1"
+ *   "kappa":  [variant names]          the multi-versioned set, in order
+ *   "map":    [{"m", "n", "k", "transA", "transB", "variant"}]  (optional)
+ *             listed shapes and the member of kappa each one takes
+ *   "tree":   [nodes]  (optional; PT_SELECT_TREE) node 0 is the root; an
+ *             inner node {"feature": 0|1|2 (log2 M, N, K), "threshold",
+ *             "left", "right"} sends feature <= threshold left; children
+ *             come after their parent; a leaf is {"variant": name}
+ *   "model":  {"transA", "transB", "coef": [10 numbers or null per kappa
+ *             member]}  (optional) predicted ln t = coef . (1, u, v, w, u^2,
+ *             v^2, w^2, uv, uw, vw), u = (log2 M - 9) / 3, v and w likewise
+ *             for N and K; used only for shapes with these transposes
+ * "method", "k" and "train_geomean" are informative.  Variant names not in
+ * this library are PT_EFORMAT. */
 int pt_load_manifest(const char *path);
 /* The variant id pt_sgemm would launch for these arguments (same rules). */
 int pt_selected_variant(char transA, char transB, int64_t M, int64_t N, int64_t K,
