@@ -123,6 +123,10 @@ int pt_variant_by_name(const char *name);
 /* The split-precision tensor-core variants (kind 1, 2) split both operands
  * into low-precision planes in a library workspace (see pt_shutdown) and run
  * tcgen05.mma with TMEM accumulators; they accept every layout and alignment.
+ * Exception: fused versions (names with "_fa" / "_fb") split A (or B) inside
+ * the GEMM kernel from the caller's matrix, so they need that operand
+ * untransposed (trans_mask), 16-byte aligned, with a leading dimension
+ * divisible by 4, and return PT_EUNSUPPORTED otherwise.
  * 3xTF32 (Markidis et al.-style split x = hi + lo, three products) and BF16x3
  * (x = b0 + b1 + b2, six products) give FP32-level error.  The paper has no
  * tensor-core versions; they are further members of the same variant space. */
