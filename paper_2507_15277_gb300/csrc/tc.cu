@@ -294,6 +294,10 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcBf16x3, 128, 3, 2, 64, 0, 1>>("tcbf16x3_m128n128_p3_sw64_fb_sk2"),
         tc_entry<Tc<kTcBf16x3, 128, 3, 4, 64, 0, 1>>("tcbf16x3_m128n128_p3_sw64_fb_sk4"),
         tc_entry<Tc<kTcBf16x3, 128, 3, 1, 64, 1, 1>>("tcbf16x3_m128n128_p3_sw64_fb_stk"),
+        // 32-column tiles: twice the CTAs of 64-column ones on skinny,
+        // long-K shapes (5-10 % faster there; more A re-reads elsewhere).
+        tc_entry<Tc<kTcBf16x3, 32, 3, 4>>("tcbf16x3_m128n32_p3_sk4"),
+        tc_entry<Tc<kTcBf16x3, 32, 3, 8>>("tcbf16x3_m128n32_p3_sk8"),
         // BF16x3 64-column tiles with room for the coalescing epilogue stage.
         tc_entry<Tc<kTcBf16x3, 64, 2>>("tcbf16x3_m128n64_p2"),
         tc_entry<Tc<kTcBf16x3, 64, 2, 4>>("tcbf16x3_m128n64_p2_sk4"),

@@ -145,7 +145,8 @@ struct Tc {
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     static constexpr uint32_t IDESC_W =
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-    static_assert(BN == 64 || BN == 128, "N of the MMA (2*BN <= 256)");
+    static_assert(BN == 32 || BN == 64 || BN == 128, "N of the MMA (2*BN <= 256, a multiple of 16)");
+    static_assert(FUSE == 0 || BN >= 64, "fused versions use 64- or 128-column tiles");
     static_assert(SPLITK == 1 || BM * RED_LD * 4 <= BAR_OFFSET, "split-K partial tile fits the pipeline memory");
     static_assert(BM % SPLITK == 0, "split-K reduction slices rows");
     // Consecutive CTAs walk GROUP_M tile rows down before moving right, so a

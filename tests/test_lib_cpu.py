@@ -48,7 +48,7 @@ def test_registry_rules():
         assert d["smem_bytes"] <= 232448
         if d["kind"] != 0:
             # split-precision tensor-core variants: 128-row tiles, TMA, any layout
-            assert d["kind"] in (1, 2) and d["bm"] == 128 and d["bn"] in (64, 128)
+            assert d["kind"] in (1, 2) and d["bm"] == 128 and d["bn"] in (32, 64, 128)
             # fused versions read B (or A) themselves: transB (transA) = 'N' only; the others take any layout
             assert d["loader"] == 1 and d["trans_mask"] == (5 if "_fb" in d["name"] else 3 if "_fa" in d["name"] else 15)
             # epilogue + producer + MMA warps (+ four converter warps when B is split in the kernel)
