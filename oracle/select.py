@@ -194,15 +194,55 @@ def model_fit(times_row, train_shapes):
     return [float(np.mean(y))] + [0.0] * (MODEL_FEATURES - 1)
 
 
-def model_pick(coefs, query):
+def model_residuals(coef, times_row, train_shapes):
+    """ln t - model at every training shape (None where the variant is
+    invalid there); None when the variant has no model."""
+    if coef is None:
+        return None
+    out = []
+    for sh, t in zip(train_shapes, times_row):
+        if np.isfinite(t) and t > 0:
+            out.append(math.log(t) - float(np.dot(np.array(coef), np.array(model_features(sh)))))
+        else:
+            out.append(None)
+    return out
+
+
+def log_distance(a, b) -> float:
+    """L1 distance of two shapes in (log2 M, log2 N, log2 K)."""
+    return sum(abs(math.log2(x) - math.log2(y)) for x, y in zip(a[:3], b[:3]))
+
+
+def model_predict(coef, query, resid=None, points=None) -> float:
+    """Predicted ln-time of one member at `query`: the quadratic model plus,
+    when residuals are given, their weighted mean over the training shapes
+    where the member is valid, with weights 1 / d^2 (d = log_distance).  A
+    query at distance 0 from valid training shapes takes the mean residual
+    of those shapes, so the prediction there is their measured ln-time."""
+    pred = float(np.dot(np.array(coef), np.array(model_features(query))))
+    if resid is None:
+        return pred
+    pts = [(log_distance(query, q), r) for q, r in zip(points, resid) if r is not None]
+    if not pts:
+        return pred
+    at = [r for d, r in pts if d == 0.0]
+    if at:
+        return pred + sum(at) / len(at)
+    num = sum(r / (d * d) for d, r in pts)
+    den = sum(1.0 / (d * d) for d, r in pts)
+    return pred + num / den
+
+
+def model_pick(coefs, query, resids=None, points=None):
     """Index of the member with the smallest predicted ln-time at `query`
-    (ties to the earlier member); None when no member has a model."""
-    f = np.array(model_features(query))
+    (ties to the earlier member); None when no member has a model.  With
+    `resids` (one list per member, aligned with `points`) the predictions
+    carry the residual correction of model_predict."""
     best, bp = None, None
     for i, c in enumerate(coefs):
         if c is None:
             continue
-        pred = float(np.dot(np.array(c), f))
+        pred = model_predict(c, query, None if resids is None else resids[i], points)
         if bp is None or pred < bp:
             best, bp = i, pred
     return best

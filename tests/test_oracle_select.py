@@ -271,3 +271,46 @@ def test_model_features_closed_form():
     # log2 512 = 9 is the centre; 4096 and 64 sit one scale unit (3 octaves) away.
     assert osel.model_features((512, 512, 512)) == [1.0] + [0.0] * 9
     assert osel.model_features((4096, 64, 512)) == [1.0, 1.0, -1.0, 0.0, 1.0, 1.0, 0.0, -1.0, 0.0, 0.0]
+
+
+def test_residual_correction_closed_forms():
+    # Intercept-only model ln t = 1 and two training shapes with residuals
+    # r1 = 0.5 at distance 1 and r2 = -1.0 at distance 2 from the query:
+    # weights 1 and 1/4, so the correction is (0.5 - 0.25) / 1.25 = 0.2.
+    coef = [1.0] + [0.0] * 9
+    q = (512, 512, 512)
+    points = [(1024, 512, 512), (512, 2048, 512)]   # log2 distances 1 and 2
+    assert osel.log_distance(q, points[0]) == 1.0 and osel.log_distance(q, points[1]) == 2.0
+    assert osel.model_predict(coef, q, [0.5, -1.0], points) == pytest.approx(1.2)
+    # an invalid point (None) does not count; one valid point gives its residual
+    assert osel.model_predict(coef, q, [None, -1.0], points) == pytest.approx(0.0)
+    # at distance 0 the prediction is that shape's measured ln t
+    times = [math.e ** 2, math.e ** 0.25]
+    res = osel.model_residuals(coef, times, points)
+    assert res == pytest.approx([1.0, -0.75])
+    assert osel.model_predict(coef, points[1], res, points) == pytest.approx(0.25)
+    # residuals of an exactly quadratic member are zero: no change to the pick
+    rng = np.random.default_rng(14)
+    shapes = _grid()
+    coefs, resids = [], []
+    for _ in range(4):
+        beta = rng.normal(0, 1, osel.MODEL_FEATURES)
+        t = [math.exp(float(np.dot(beta, osel.model_features(s)))) for s in shapes]
+        c = osel.model_fit(t, shapes)
+        coefs.append(c)
+        resids.append(osel.model_residuals(c, t, shapes))
+        assert np.allclose([r for r in resids[-1]], 0.0, atol=1e-9)
+    for q in [(300, 700, 2000), (128, 4096, 200), (5000, 100, 900)]:
+        assert osel.model_pick(coefs, q, resids, shapes) == osel.model_pick(coefs, q)
+
+
+def test_residual_correction_can_change_the_pick():
+    # Two members with the same model; member 1 is measured 0.3 faster than
+    # its model at the training shape next to the query and 0.3 slower far
+    # away, so the nearby residual wins and member 1 is picked.
+    coef = [0.0] * 10
+    points = [(512, 512, 1024), (4096, 4096, 128)]
+    q = (512, 512, 2048)                      # distances 1 and 3 + 3 + 4 = 10
+    resids = [[0.0, 0.0], [-0.3, 0.3]]
+    assert osel.model_pick([coef, coef], q) == 0          # a tie without residuals
+    assert osel.model_pick([coef, coef], q, resids, points) == 1
