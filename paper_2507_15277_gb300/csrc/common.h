@@ -69,6 +69,13 @@ struct Manifest {
     // applies to shapes with transposes (model_ta, model_tb).
     std::vector<std::vector<double>> coef;
     char model_ta = 0, model_tb = 0;
+    // Optional residual correction of the model: the training shapes
+    // (model_pts) and, per member, ln t - model at each of them (resid[i][j];
+    // NaN where the member is invalid; resid[i] empty: no correction).  The
+    // prediction at an unlisted shape adds the 1/d^2-weighted mean of the
+    // member's residuals, d the L1 distance in (log2 M, log2 N, log2 K).
+    std::vector<pt_shape_t> model_pts;
+    std::vector<std::vector<double>> resid;
     double train_geomean = 0;
 };
 

@@ -654,6 +654,33 @@ static std::vector<double> fit_member(const std::vector<pt_shape_t> &shapes, con
     return c;
 }
 
+// ln t - model at every training shape (NaN where the member is invalid);
+// empty when the member has no model.
+static std::vector<double> member_residuals(const std::vector<double> &coef, const std::vector<pt_shape_t> &shapes,
+                                            const std::vector<double> &times) {
+    std::vector<double> r;
+    if (coef.empty()) return r;
+    for (size_t j = 0; j < shapes.size(); ++j) {
+        if (!std::isfinite(times[j]) || times[j] <= 0) {
+            r.push_back(std::nan(""));
+            continue;
+        }
+        double f[kModelFeatures];
+        model_features(shapes[j], f);
+        double pred = 0;
+        for (int i = 0; i < kModelFeatures; ++i) pred += coef[i] * f[i];
+        r.push_back(std::log(times[j]) - pred);
+    }
+    return r;
+}
+
+// L1 distance of two shapes in (log2 M, log2 N, log2 K).
+static double log_distance(const pt_shape_t &a, const pt_shape_t &b) {
+    return std::fabs(std::log2((double)a.m) - std::log2((double)b.m)) +
+           std::fabs(std::log2((double)a.n) - std::log2((double)b.n)) +
+           std::fabs(std::log2((double)a.k) - std::log2((double)b.k));
+}
+
 // ---- manifest --------------------------------------------------------------------
 static std::string shape_json(const pt_shape_t &s) {
     char buf[160];
@@ -664,7 +691,8 @@ static std::string shape_json(const pt_shape_t &s) {
 
 static int write_manifest(const char *path, const char *method, int k, double g, const std::vector<int> &kappa_ids,
                           const std::vector<std::pair<pt_shape_t, int>> &map, const std::vector<TreeNode> *tree,
-                          const std::vector<std::vector<double>> *coef, char ta, char tb) {
+                          const std::vector<std::vector<double>> *coef, char ta, char tb,
+                          const std::vector<pt_shape_t> *pts, const std::vector<std::vector<double>> *resid) {
     std::ofstream o(path);
     if (!o) return set_error(PT_EIO, 9, "cannot write manifest '%s'", path);
     auto name = [](int id) {
@@ -714,7 +742,35 @@ static int write_manifest(const char *path, const char *method, int k, double g,
             }
             o << "]";
         }
-        o << "\n  ]}";
+        o << "\n  ]";
+        if (pts && resid && resid->size() == coef->size()) {
+            // Residual correction: the training shapes and each member's
+            // ln t - model at them (null where it is invalid).
+            o << ",\n  \"points\": [";
+            for (size_t j = 0; j < pts->size(); ++j)
+                o << (j ? ", " : "") << "[" << (long long)(*pts)[j].m << ", " << (long long)(*pts)[j].n << ", "
+                  << (long long)(*pts)[j].k << "]";
+            o << "],\n  \"resid\": [";
+            for (size_t i = 0; i < resid->size(); ++i) {
+                o << (i ? ",\n" : "\n") << "    ";
+                if ((*resid)[i].empty()) {
+                    o << "null";
+                    continue;
+                }
+                o << "[";
+                for (size_t j = 0; j < (*resid)[i].size(); ++j) {
+                    char buf[40];
+                    if (std::isfinite((*resid)[i][j]))
+                        std::snprintf(buf, sizeof(buf), "%.17g", (*resid)[i][j]);
+                    else
+                        std::snprintf(buf, sizeof(buf), "null");
+                    o << (j ? ", " : "") << buf;
+                }
+                o << "]";
+            }
+            o << "\n  ]";
+        }
+        o << "}";
     }
     o << "\n}\n";
     o.flush();
@@ -822,6 +878,49 @@ int read_manifest(const char *path, Manifest *out) {
             }
             m.coef.push_back(std::move(c));
         }
+        const json::Value *pv = md->get("points"), *rv = md->get("resid");
+        if (pv || rv) {
+            if (!pv || !rv || pv->kind != json::Value::Array || rv->kind != json::Value::Array ||
+                rv->arr.size() != m.kappa.size())
+                return set_error(PT_EFORMAT, 1, "manifest: malformed model residuals");
+            for (const auto &e : pv->arr) {
+                if (e.kind != json::Value::Array || e.arr.size() != 3)
+                    return set_error(PT_EFORMAT, 1, "manifest: bad model point");
+                double d[3];
+                for (int q = 0; q < 3; ++q) {
+                    if (e.arr[q].kind != json::Value::Number || !(e.arr[q].num >= 1))
+                        return set_error(PT_EFORMAT, 1, "manifest: bad model point");
+                    d[q] = e.arr[q].num;
+                }
+                pt_shape_t sh;
+                sh.m = (int64_t)d[0];
+                sh.n = (int64_t)d[1];
+                sh.k = (int64_t)d[2];
+                sh.transA = m.model_ta;
+                sh.transB = m.model_tb;
+                m.model_pts.push_back(sh);
+            }
+            for (size_t i = 0; i < rv->arr.size(); ++i) {
+                const json::Value &e = rv->arr[i];
+                std::vector<double> r;
+                if (e.kind == json::Value::Array) {
+                    if (e.arr.size() != m.model_pts.size() || m.coef[i].empty())
+                        return set_error(PT_EFORMAT, 1, "manifest: bad residual row");
+                    for (const auto &x : e.arr) {
+                        if (x.kind == json::Value::Null) {
+                            r.push_back(std::nan(""));
+                        } else if (x.kind == json::Value::Number && std::isfinite(x.num)) {
+                            r.push_back(x.num);
+                        } else {
+                            return set_error(PT_EFORMAT, 1, "manifest: bad residual");
+                        }
+                    }
+                } else if (e.kind != json::Value::Null) {
+                    return set_error(PT_EFORMAT, 1, "manifest: bad residual row");
+                }
+                m.resid.push_back(std::move(r));
+            }
+        }
     }
     *out = std::move(m);
     return PT_OK;
@@ -854,6 +953,29 @@ int manifest_pick(const Manifest &m, const pt_shape_t &s) {
             if (m.coef[i].empty()) continue;
             double pred = 0;
             for (int j = 0; j < kModelFeatures; ++j) pred += m.coef[i][j] * f[j];
+            if (i < m.resid.size() && !m.resid[i].empty()) {
+                // Residual correction: 1/d^2-weighted mean of the member's
+                // residuals at its valid training shapes; at distance 0 the
+                // mean of those shapes' residuals (their measured ln t).
+                double num = 0, den = 0, at = 0;
+                int n_at = 0;
+                for (size_t j = 0; j < m.model_pts.size(); ++j) {
+                    const double r = m.resid[i][j];
+                    if (!std::isfinite(r)) continue;
+                    const double d = log_distance(s, m.model_pts[j]);
+                    if (d == 0.0) {
+                        at += r;
+                        ++n_at;
+                    } else {
+                        num += r / (d * d);
+                        den += 1.0 / (d * d);
+                    }
+                }
+                if (n_at > 0)
+                    pred += at / n_at;
+                else if (den > 0)
+                    pred += num / den;
+            }
             if (pred < bp) {
                 bp = pred;
                 best = m.kappa[i];
@@ -989,22 +1111,24 @@ int pt_select(const char *table_path, const int *train_idx, int n_train, int k, 
             if (best >= 0) map.emplace_back(t.shapes[shapes[j]], best);
         }
         // Time model over the training shapes, when they share one transpose pair.
-        std::vector<std::vector<double>> coef;
+        std::vector<std::vector<double>> coef, resid;
+        std::vector<pt_shape_t> tr;
         bool one_pair = true;
         for (int j = 1; j < p.S; ++j)
             one_pair = one_pair && t.shapes[shapes[j]].transA == t.shapes[shapes[0]].transA &&
                        t.shapes[shapes[j]].transB == t.shapes[shapes[0]].transB;
         if (one_pair) {
-            std::vector<pt_shape_t> tr;
             for (int j = 0; j < p.S; ++j) tr.push_back(t.shapes[shapes[j]]);
             for (int c : set) {
                 std::vector<double> tv;
                 for (int j = 0; j < p.S; ++j) tv.push_back(t.t[p.cand[c]][shapes[j]]);
                 coef.push_back(fit_member(tr, tv));
+                resid.push_back(member_residuals(coef.back(), tr, tv));
             }
         }
         rc = write_manifest(manifest_path, mname, k, val, ids, map, method == PT_SELECT_TREE ? &tree : nullptr,
-                            one_pair ? &coef : nullptr, t.shapes[shapes[0]].transA, t.shapes[shapes[0]].transB);
+                            one_pair ? &coef : nullptr, t.shapes[shapes[0]].transA, t.shapes[shapes[0]].transB,
+                            one_pair ? &tr : nullptr, one_pair ? &resid : nullptr);
         if (rc != PT_OK) return rc;
     }
     return PT_OK;

@@ -118,10 +118,11 @@ def test_manifest_drives_pt_sgemm(small_table, tmp_path):
         kappa = [pt.variant_by_name(n) for n in m["kappa"]]
         coefs = m["model"]["coef"] if "model" in m else None
         if coefs is not None:
-            f = np.array(osel.model_features(q))
-            preds = sorted(float(np.dot(c, f)) for c in coefs if c is not None)
+            resids, points = m["model"].get("resid"), m["model"].get("points")
+            preds = sorted(osel.model_predict(c, q, None if resids is None else r, points)
+                           for c, r in zip(coefs, resids or [None] * len(coefs)) if c is not None)
             if len(preds) < 2 or preds[1] - preds[0] > 1e-9:  # a near tie admits either member
-                assert pt.selected_variant(*q) == kappa[osel.model_pick(coefs, q)]
+                assert pt.selected_variant(*q) == kappa[osel.model_pick(coefs, q, resids, points)]
         else:
             idx = osel.nearest_shape(q, shapes)
             assert pt.selected_variant(*q) == pt.selected_variant(*shapes[idx])

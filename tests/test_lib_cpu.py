@@ -347,21 +347,29 @@ def test_time_model_matches_oracle(seed, tmp_path):
     ids, _ = pt.select(path, train, 4, manifest=man)
     ids = [i for i in ids if i >= 0]
     m = json.load(open(man))
-    coefs = [osel.model_fit(t[v, train], [shapes[s][:3] for s in train]) for v in ids]
+    points = [shapes[s][:3] for s in train]
+    coefs = [osel.model_fit(t[v, train], points) for v in ids]
+    resids = [osel.model_residuals(c, t[v, train], points) for c, v in zip(coefs, ids)]
     for got, want in zip(m["model"]["coef"], coefs):
         if want is None:
             assert got is None
         else:
             assert np.allclose(got, want, rtol=1e-8, atol=1e-8)
+    assert [tuple(p) for p in m["model"]["points"]] == [tuple(p) for p in points]
+    for got, want in zip(m["model"]["resid"], resids):
+        if want is None:
+            assert got is None
+            continue
+        assert [g is None for g in got] == [w is None for w in want]
+        assert np.allclose([g for g in got if g is not None], [w for w in want if w is not None], atol=1e-8)
     pt.load_manifest(man)
     try:
         # extents divisible by 16, so that every variant's alignment rules admit them
         for q in [(208, 704, 3008), (128, 4096, 304), (3008, 160, 160), (784, 784, 784), (112, 112, 5008)]:
-            f = np.array(osel.model_features(q))
-            preds = sorted(float(np.dot(c, f)) for c in coefs if c is not None)
+            preds = sorted(osel.model_predict(c, q, r, points) for c, r in zip(coefs, resids) if c is not None)
             if len(preds) > 1 and preds[1] - preds[0] < 1e-9:
                 continue  # a near tie: either member is a correct pick
-            assert pt.selected_variant(*q) == ids[osel.model_pick(coefs, q)]
+            assert pt.selected_variant(*q) == ids[osel.model_pick(coefs, q, resids, points)]
         # listed shapes keep their fastest member
         s = train[5]
         assert pt.selected_variant(*shapes[s][:3]) == osel.best_in_set(t, ids, s)
@@ -389,7 +397,8 @@ def test_manifest_without_model_uses_nearest_shape(tmp_path):
 
 def test_malformed_time_model_is_rejected(tmp_path):
     # Planted mistakes in the manifest's model block: each must fail to load
-    # with PT_EFORMAT; a block whose only change is a null row loads.
+    # with PT_EFORMAT; a member without a model, or a model without residuals,
+    # loads.
     levels = (128, 512, 1024, 4096)
     shapes = [(m, n, k, "N", "N") for m in levels for n in levels for k in levels]
     t = random_table(7, 6, len(shapes), invalid=0.0)
@@ -416,13 +425,22 @@ def test_malformed_time_model_is_rejected(tmp_path):
         lambda md: md.__setitem__("transA", "NN"),        # not one character
         lambda md: md.pop("transB"),                      # missing field
         lambda md: md["coef"].__setitem__(1, 3.0),        # row neither a list nor null
+        lambda md: md["resid"].pop(),                     # one residual row fewer than kappa
+        lambda md: md["resid"][0].pop(),                  # a row shorter than the point list
+        lambda md: md["resid"][0].__setitem__(2, "x"),    # not a number
+        lambda md: md["points"][0].pop(),                 # a point without K
+        lambda md: md["points"].__setitem__(1, [0, 512, 512]),  # a point with M = 0
+        lambda md: md.pop("points"),                      # residuals without their points
+        lambda md: md["coef"].__setitem__(0, None),       # residuals for a member without a model
     ]
     for fn in bad:
         with pytest.raises(pt.PtError) as e:
             pt.load_manifest(mutated(fn))
         assert e.value.code == _lib.PT_EFORMAT
-    # A member without a model (null row) is allowed.
-    ok = mutated(lambda md: md["coef"].__setitem__(0, None))
+    # A member without a model (null coefficient and residual rows) is
+    # allowed, and so is a model without residuals.
+    ok = mutated(lambda md: (md["coef"].__setitem__(0, None), md["resid"].__setitem__(0, None)))
+    pt.load_manifest(mutated(lambda md: (md.pop("points"), md.pop("resid"))))
     pt.load_manifest(ok)
     try:
         assert pt.selected_variant(208, 704, 3008) in ids
