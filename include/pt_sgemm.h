@@ -55,9 +55,10 @@ int pt_last_error_arg(void);
  * that shape.  Any other shape goes, in this order, to the manifest's
  * regression tree (PT_SELECT_TREE manifests), else to its time model (one
  * least-squares quadratic in (log2 M, log2 N, log2 K) of ln t per member,
- * fitted on the training shapes when they share one transpose pair and used
- * only for queries with that pair: the member of least predicted time, ties
- * to the earlier member), else to the pick of the nearest listed shape in
+ * corrected by the distance-weighted mean of its residuals at the training
+ * shapes, fitted when they share one transpose pair and used only for
+ * queries with that pair: the member of least predicted time, ties to the
+ * earlier member), else to the pick of the nearest listed shape in
  * (log2 M, log2 N, log2 K), L1 distance, ties to the lower entry.  With no
  * manifest loaded, or when the picked variant cannot run the arguments
  * (alignment, transpose support), the next members of kappa are tried in
@@ -211,9 +212,14 @@ int pt_table_shape(const char *table_path, int i, pt_shape_t *out);
  *             "left", "right"} sends feature <= threshold left; children
  *             come after their parent; a leaf is {"variant": name}
  *   "model":  {"transA", "transB", "coef": [10 numbers or null per kappa
- *             member]}  (optional) predicted ln t = coef . (1, u, v, w, u^2,
+ *             member], "points": [[M, N, K]], "resid": [[number or null per
+ *             point] or null per member]}  (optional; "points" and "resid"
+ *             optional together) predicted ln t = coef . (1, u, v, w, u^2,
  *             v^2, w^2, uv, uw, vw), u = (log2 M - 9) / 3, v and w likewise
- *             for N and K; used only for shapes with these transposes
+ *             for N and K, plus the 1/d^2-weighted mean of the member's
+ *             residuals at the points (d: L1 distance in log2 M, N, K; at
+ *             d = 0 the mean of the residuals there); used only for shapes
+ *             with these transposes
  * "method", "k" and "train_geomean" are informative.  Variant names not in
  * this library are PT_EFORMAT. */
 int pt_load_manifest(const char *path);
