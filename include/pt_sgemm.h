@@ -168,7 +168,7 @@ int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids,
 
 #define PT_SELECT_EXACT 0       /* enumerate every k-subset                    */
 #define PT_SELECT_GREEDY_SWAP 1 /* greedy growth + 1-swap local search         */
-#define PT_SELECT_AUTO 2        /* exact when C(n,k) <= 2e6, else greedy+swap  */
+#define PT_SELECT_AUTO 2        /* exact when C(n,k) <= 2e7, else greedy+swap  */
 #define PT_SELECT_KMEANS 3      /* k-means on performance vectors (IV-C-2)     */
 #define PT_SELECT_TREE 4        /* regression tree with k leaves (IV-C-3)      */
 

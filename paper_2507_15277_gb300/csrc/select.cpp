@@ -1071,7 +1071,7 @@ int pt_select(const char *table_path, const int *train_idx, int n_train, int k, 
             select_greedy_swap(p, k, seed, &set, &val);
             break;
         case PT_SELECT_AUTO:
-            if (k >= (int)p.cand.size() || log_binom((int)p.cand.size(), k) <= std::log(2e6)) {
+            if (k >= (int)p.cand.size() || log_binom((int)p.cand.size(), k) <= std::log(2e7)) {
                 select_exact(p, k, &set, &val);
             } else {
                 mname = "greedy_swap";
