@@ -191,14 +191,17 @@ def test_score_best_of_set_and_selector(tmp_path):
     # best-of-set scoring == Eq. 1 on the held-out shapes
     assert pt.score(path, held, ids) == pytest.approx(osel.set_performance(t, ids, held), rel=1e-12)
     # selector-realised: each held-out shape takes the member with the smallest
-    # time predicted by the manifest's model (fitted on the training shapes)
+    # time predicted by the manifest's model (fitted on the training shapes,
+    # corrected by the distance-weighted residuals there)
     m = json.load(open(man))
     assert [e["variant"] for e in m["map"]] == [names[osel.best_in_set(t, ids, s)] for s in train]
     tb = osel.per_shape_best(t)
     logs = []
-    coefs = [osel.model_fit(t[v, train], [shapes[s] for s in train]) for v in ids]
+    points = [shapes[s][:3] for s in train]
+    coefs = [osel.model_fit(t[v, train], points) for v in ids]
+    resids = [osel.model_residuals(c, t[v, train], points) for c, v in zip(coefs, ids)]
     for s in held:
-        v = ids[osel.model_pick(coefs, shapes[s][:3])]
+        v = ids[osel.model_pick(coefs, shapes[s][:3], resids, points)]
         tv = t[v, s]
         if not np.isfinite(tv):
             fall = [t[i, s] for i in ids if np.isfinite(t[i, s])]
@@ -444,5 +447,33 @@ def test_malformed_time_model_is_rejected(tmp_path):
     pt.load_manifest(ok)
     try:
         assert pt.selected_variant(208, 704, 3008) in ids
+    finally:
+        pt.load_manifest(None)
+
+
+def test_residuals_decide_between_equal_models(tmp_path):
+    # Two members with identical models; member 1 runs 0.3 faster than its
+    # model at the training shape next to the query and 0.3 slower at the far
+    # one, so the library must pick it (without residuals: a tie, member 0).
+    simt = [pt.variant(i)["name"] for i in range(pt.num_variants())
+            if pt.variant(i)["kind"] == 0 and pt.variant(i)["trans_mask"] == 15 and pt.variant(i)["vec"] == 1][:2]
+    zero = [0.0] * 10
+    man = {"format": "pt-manifest-1", "kappa": simt,
+           "map": [{"m": 4096, "n": 4096, "k": 128, "transA": "N", "transB": "N", "variant": simt[0]}],
+           "model": {"transA": "N", "transB": "N", "coef": [zero, zero],
+                     "points": [[512, 512, 1024], [4096, 4096, 128]], "resid": [[0.0, 0.0], [-0.3, 0.3]]}}
+    path = str(tmp_path / "m.json")
+    json.dump(man, open(path, "w"))
+    pt.load_manifest(path)
+    try:
+        assert pt.selected_variant(512, 512, 2048) == pt.variant_by_name(simt[1])
+        # (4096, 4096, 256) is at distance 1 from the second point and 8 from
+        # the first: member 1's correction is (-0.3/64 + 0.3) / (1/64 + 1) > 0,
+        # so member 0 wins there
+        assert pt.selected_variant(4096, 4096, 256) == pt.variant_by_name(simt[0])
+        del man["model"]["points"], man["model"]["resid"]
+        json.dump(man, open(path, "w"))
+        pt.load_manifest(path)
+        assert pt.selected_variant(512, 512, 2048) == pt.variant_by_name(simt[0])  # a tie: the earlier member
     finally:
         pt.load_manifest(None)
