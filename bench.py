@@ -651,6 +651,87 @@ def cpu_oracle_sample(shapes, rows_per_shape, seed_base=1000):
     return flops / dt / 1e12, dt, og.num_threads(), flops
 
 
+KIND_LABELS = {0: "fp32_simt", 1: "3xtf32", 2: "bf16x3"}
+
+
+def selection_by_kind(pt, table, train, held, out_dir):
+    """PortabilityTune (Eq. 1) run on one kind's variants at a time: the
+    table restricted to FP32 SIMT, 3xTF32 or BF16x3 rows.  For k = 1, 2, 4, 8
+    the held-out geomean of t_best / t(best member) is scored against that
+    kind's own per-shape best and against the per-shape best of the whole
+    family (every kind meets the same 2e-6 error bound)."""
+    import csv
+    with open(table) as f:
+        rows = list(csv.DictReader(f))
+    fields = list(rows[0].keys()) if rows else []
+    kind_of = {}
+    out = {}
+    for kind, label in KIND_LABELS.items():
+        sub = []
+        for r in rows:
+            if r["variant"] not in kind_of:
+                kind_of[r["variant"]] = pt.variant(pt.variant_by_name(r["variant"]))["kind"]
+            if kind_of[r["variant"]] == kind:
+                sub.append(r)
+        if not sub:
+            continue
+        path = os.path.join(out_dir, "table_%s.csv" % label)
+        with open(path, "w", newline="") as f:
+            w = csv.DictWriter(f, fieldnames=fields)
+            w.writeheader()
+            w.writerows(sub)
+        res = {"variants": len({r["variant"] for r in sub})}
+        for k in (1, 2, 4, 8):
+            ids, _ = pt.select(path, train, k)
+            res["k%d" % k] = {"own_best_pct": round(100 * pt.score(path, held, ids), 2),
+                              "family_best_pct": round(100 * pt.score(table, held, ids), 2)}
+        out[label] = res
+    return out
+
+
+def best_simt_from_table(pt, table, shape=(4096, 4096, 4096)):
+    """Fastest FP32 SIMT variant of the timing table on one shape (median)."""
+    import csv
+    best = None
+    with open(table) as f:
+        for r in csv.DictReader(f):
+            if (int(r["M"]), int(r["N"]), int(r["K"])) != shape or not int(r["valid"]):
+                continue
+            if pt.variant(pt.variant_by_name(r["variant"]))["kind"] != 0:
+                continue
+            if best is None or float(r["median_ms"]) < best[1]:
+                best = (r["variant"], float(r["median_ms"]))
+    return best
+
+
+def config1_timing(pt, dev, stream, reps=200):
+    """The fixed single-GEMM workload: 256^3, NN, alpha = 1, beta = 0, U[-1,1]
+    (seeds 1 and 2), the 128x128x8 cp.async variant; mean of `reps` launches
+    replayed from a CUDA graph, CUDA events."""
+    import torch
+    from workloads import matrix
+    name = "s128x128x8_w32x64_t8x8_kl1_v4_p2_sk1_cpm"
+    vid = pt.variant_by_name(name)
+    A = torch.from_numpy(matrix("uniform", 1, 256, 256)).to(dev)
+    B = torch.from_numpy(matrix("uniform", 2, 256, 256)).to(dev)
+    C = torch.empty((256, 256), device=dev)
+    with torch.cuda.stream(stream):
+        pt.sgemm(A, B, C, variant=vid, stream=stream)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(reps):
+                pt.sgemm(A, B, C, variant=vid, stream=stream)
+        g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return name, ms
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -773,6 +854,7 @@ def main():
                     "heldout_selector_pct": 100 * pt.score(table, held, mode=pt.PT_SCORE_SELECTOR, manifest=man),
                     "select_s": dt}
         info["selectors"] = comp
+        info["by_kind"] = selection_by_kind(pt, table, train, held, out_dir)
     manifest = os.path.join(out_dir, "kappa_k%d.json" % args.k)
     share_manifest(pt, manifest, rank, world, collect_and_select)
 
@@ -997,6 +1079,8 @@ def main():
                     "fp32_equivalent_tflops": flops[dom] / (dom_ms * 1e-3) / 1e12,
                     "fp32_equivalent_frac_of_fp32_peak": flops[dom] / (dom_ms * 1e-3) / 1e12 / fp32_peak}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    # The whole call (split kernel + GEMM kernel for the tensor-core versions).
+    roofline["call_frac"] = roofline["achieved"] * dom_ms / call_ms / roofline["peak"]
     roofline.update({"traffic": traffic_for(dvar["name"], (M, N, K)), "kernel": dvar["name"], "shape": [M, N, K],
                      "kernel_ms": dom_ms, "launches_timed": n_timed, "call_ms": call_ms,
                      "split_ms": (call_ms - dom_ms) if dvar["kind"] != 0 else 0.0,
@@ -1013,6 +1097,20 @@ def main():
     cub_ms, _ = per_shape_times(
         [lambda i=i: torch.matmul(devA[i], devB[i], out=devC[i]) for i in range(len(shapes))], stream)
     cublas_tflops = step_flops / (sum(cub_ms) * 1e-3) / 1e12
+
+    c1_name, c1_ms = config1_timing(pt, dev, stream)
+    bf16_peak = peaks.get("bf16_tflops") or 1900.0
+
+    def fracs(p, tf):
+        kind = pt.variant(p)["kind"]
+        d = {"frac_fp32_peak": round(tf / fp32_peak, 4)}
+        if kind:
+            nprod, ratio = (3, 1.1 / 2.25) if kind == 1 else (6, 1.0)
+            d["frac_tensor_peak"] = round(nprod * tf / (bf16_peak * ratio), 4)
+        return d
+
+    best_simt = best_simt_from_table(pt, table)
+    small = [i for i in range(len(shapes)) if flops[i] <= 1.1e9]
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -1031,8 +1129,8 @@ def main():
                    "train_split": "parity (i_m+i_n+i_k even) 32/32",
                    "l2": "inputs 1.6 GB (> 129 MB L2) read once per step; no flush needed",
                    "timed": "CUDA graph of the 64 pt_sgemm launches, replayed per step",
-                   "compute": "FP32 operands and results; FP32 FMA (SIMT variants) or BF16x3 / 3xTF32 tensor-core "
-                              "splits with FP32 accumulation, whichever the selector picks per shape",
+                   "compute": "FP32 in/out; per shape the selector picks FP32-FMA SIMT or BF16x3/3xTF32 tensor-core "
+                              "splits with FP32 accumulation",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "clocks": clk,
         "gpu_launches": args.steps * sum(1 if pt.variant(p)["kind"] == 0 else 2 for p in picks),
@@ -1052,10 +1150,20 @@ def main():
         "kappa": sel.get(args.k, {}).get("names"),
         "selectors": info.get("selectors"),
         "tuning": {"tune_s": info.get("tune_s"), "select_s": info.get("select_s"), "table": table},
-        "per_shape": [{"shape": list(s), "ms": round(ms, 5), "tflops": round(f / (ms * 1e-3) / 1e12, 3),
-                       "gbs": round(4.0 * (s[0] * s[2] + s[2] * s[1] + s[0] * s[1]) / (ms * 1e-3) / 1e9, 1),
-                       "variant": pt.variant(p)["name"], "cublas_tflops": round(f / (cm * 1e-3) / 1e12, 3)}
+        "per_shape": [dict({"shape": list(s), "ms": round(ms, 5), "tflops": round(f / (ms * 1e-3) / 1e12, 3),
+                            "gbs": round(4.0 * (s[0] * s[2] + s[2] * s[1] + s[0] * s[1]) / (ms * 1e-3) / 1e9, 1),
+                            "variant": pt.variant(p)["name"], "cublas_tflops": round(f / (cm * 1e-3) / 1e12, 3)},
+                           **fracs(p, f / (ms * 1e-3) / 1e12))
                       for s, ms, f, p, cm in zip(shapes, shape_ms, flops, picks, cub_ms)],
+        "small_shapes": {"count": len(small), "max_gflop": 1.1, "sum_ms": sum(shape_ms[i] for i in small),
+                         "sum_ms_all": sum(shape_ms)},
+        "config1": {"workload": "256^3 NN, alpha=1, beta=0, U[-1,1], fixed 128x128x8 variant", "variant": c1_name,
+                    "ms": c1_ms, "tflops": 2.0 * 256 ** 3 / (c1_ms * 1e-3) / 1e12,
+                    "frac_fp32_peak": 2.0 * 256 ** 3 / (c1_ms * 1e-3) / 1e12 / fp32_peak},
+        "best_fp32_simt_4096": None if best_simt is None else {
+            "variant": best_simt[0], "ms": best_simt[1], "tflops": 2.0 * 4096 ** 3 / (best_simt[1] * 1e-3) / 1e12,
+            "frac_fp32_peak": 2.0 * 4096 ** 3 / (best_simt[1] * 1e-3) / 1e12 / fp32_peak},
+        "selection_by_kind": info.get("by_kind"),
         "context": {"per_shape_timing": per_shape_timing, "cublas_sgemm_tflops": cublas_tflops, "cublas_math": "FP32 (allow_tf32=False, precision highest)",
                     "per_shape_wins_vs_cublas": sum(1 for m, c in zip(shape_ms, cub_ms) if m <= c),
                     "sum_ms_ours": sum(shape_ms), "sum_ms_cublas": sum(cub_ms),

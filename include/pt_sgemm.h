@@ -69,9 +69,11 @@ int pt_sgemm(char transA, char transB, int64_t M, int64_t N, int64_t K,
              float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
              float beta, float *C, int64_t ldc, void *stream);
 
-/* Runs variant `id` (0 <= id < pt_num_variants()).  PT_EUNSUPPORTED when the
- * variant's layout or alignment rules exclude these arguments; nothing is
- * launched then. */
+/* Runs variant `id` (0 <= id < pt_num_variants()): one code variant, i.e.
+ * one configuration of the kernel's parameters compiled ahead of time
+ * (Section III-A).  The tuner, the tests and single-variant callers use it.
+ * PT_EUNSUPPORTED when the variant's layout or alignment rules exclude these
+ * arguments; nothing is launched then. */
 int pt_sgemm_variant(int id, char transA, char transB, int64_t M, int64_t N, int64_t K,
                      float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
                      float beta, float *C, int64_t ldc, void *stream);
@@ -150,6 +152,9 @@ typedef struct pt_tune_opts {
     double tol;          /* screening bound on the normalised error (2e-6)     */
     int64_t pool_bytes;  /* rotating input pool; >= 2x L2 keeps L2 cold        */
     int verbose;         /* progress to stderr                                 */
+    int64_t fail_launch; /* test hook: the n-th variant launch of this call
+                            (1-based; screening and timed launches count)
+                            is not made and reports PT_ECUDA; 0 = off      */
 } pt_tune_opts_t;
 
 /* Fills *o with the defaults above. */
@@ -159,7 +164,9 @@ void pt_tune_default_opts(pt_tune_opts_t *o);
  * all) on every shape and appends one CSV row per (shape, variant) to
  * table_path, flushing after each row, so the file is the checkpoint.  Each
  * variant is first screened against the reference kernel on the same inputs;
- * a launch error or a normalised error above opts->tol marks the row invalid.
+ * a launch error or a normalised error above opts->tol marks the row invalid
+ * (status column = the error) and tuning goes on with the next variant; only
+ * an error that leaves the CUDA context unusable stops it (PT_ECUDA).
  * Timing: per-launch CUDA events after warmup, inputs rotating through a pool
  * larger than L2; median and mean recorded.  The library allocates and frees
  * its own device buffers on the current device.  Synchronous. */
@@ -192,7 +199,15 @@ int pt_select(const char *table_path, const int *train_idx, int n_train, int k,
 #define PT_SCORE_SELECTOR 1     /* each shape uses the runtime selector's pick
                                    from the manifest at manifest_path         */
 
-/* Geomean over the listed shapes of t_best(s) / t(chosen(s), s). */
+/* Held-out scoring (Section V-E): the geometric mean over the listed shapes
+ * (indices into the table's distinct-shape list) of t_best(s) / t(chosen(s), s),
+ * the reciprocal of the paper's slowdown over Oracle (S/O), with t_best over
+ * every valid variant of the table.  chosen(s) is kappa's fastest member on s
+ * (PT_SCORE_BEST_OF_SET, ids[0..k), the paper's measure) or the runtime
+ * selector's pick from the manifest (PT_SCORE_SELECTOR; ids unused; where the
+ * pick has no valid time, pt_sgemm's fallback order: the other members, then
+ * the default variant).  If some listed shape has no valid time left, the
+ * geomean is 0.  CPU only. */
 int pt_score(const char *table_path, const int *ids, int k, const int *shape_idx,
              int n, int mode, const char *manifest_path, double *out_geomean);
 
@@ -200,7 +215,8 @@ int pt_score(const char *table_path, const int *ids, int k, const int *shape_idx
 int pt_table_shapes(const char *table_path, int *out_n);
 int pt_table_shape(const char *table_path, int i, pt_shape_t *out);
 
-/* Installs the manifest used by pt_sgemm (process-wide, mutex-guarded);
+/* Installs the multi-versioned set and the classifier that picks from it at
+ * run time (Fig. 1, Section III-C) for pt_sgemm (process-wide, mutex-guarded);
  * NULL clears it.  PT_EIO when the file cannot be read, PT_EFORMAT when it
  * is not a manifest of this form (one JSON object; pt_select writes it):
  *   "format": "pt-manifest-1"
@@ -280,20 +296,27 @@ int pt_shutdown(void);
  * loops in which an allocation (that may synchronise the device) is not
  * acceptable, and hosts that only run with memory reserved in advance.
  * Same operation and arguments as pt_sgemm; it always runs the 3xTF32
- * tensor-core kernel (128 x 128 tiles), with the split planes in a fixed
- * array of PT_NOALLOC_SCRATCH_BYTES bytes of device memory that belongs to
- * the library image (every GPU that loads the library holds it until the
- * process exits).  It calls no cudaMalloc, cudaFree or allocating routine.
+ * tensor-core kernel of the registry's tc3xtf32_m128n128_p3 (128 x 128
+ * tiles, one CTA per SM) and gives the same bits, with the split planes in a
+ * fixed array of PT_NOALLOC_SCRATCH_BYTES bytes of device memory that belongs
+ * to the library image.  It calls no cudaMalloc, cudaFree or allocating
+ * routine.
  * Limit: 2 * (M + N) * round_up(K, 8) * 4 bytes (plus up to 1 KiB of
  * alignment) must not exceed PT_NOALLOC_SCRATCH_BYTES, else PT_EINVAL and
- * nothing is launched.  The first call on a device looks up the array's
- * device address on that device (the device must be current) and sets the
- * kernel's shared-memory attribute; make that first call before any other
- * use on the device that must not do such set-up.  Every call shares the one
- * array: calls whose kernels overlap on the GPU (e.g. on two streams without
- * ordering between them) race on it and give wrong results.  A bounded
- * device wait that gives up leaves C unwritten (not reported through
- * pt_device_status). */
+ * nothing is launched.
+ * First call on a device (that device current): under CUDA's default lazy
+ * module loading it loads the library module that holds the array, which
+ * commits the PT_NOALLOC_SCRATCH_BYTES of device memory at that moment (with
+ * CUDA_MODULE_LOADING=EAGER this already happened when the context was
+ * created); it also looks up the array's device address and sets the
+ * kernel's shared-memory attribute.  Make that first call (any small shape)
+ * at start-up, before a pool allocator takes the device's free memory and
+ * before any stream capture; it returns PT_ECUDA if the memory is not free.
+ * Later calls on the device allocate nothing.
+ * Every call shares the one array and leaves its planes there: calls whose
+ * kernels overlap on the GPU (e.g. on two streams without ordering between
+ * them) race on it and give wrong results.  A bounded device wait that gives
+ * up leaves C unwritten and is reported by pt_device_status. */
 #define PT_NOALLOC_SCRATCH_BYTES (64u << 20)
 int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K,
                             float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
@@ -303,6 +326,19 @@ int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int64_t N, int6
  * (PT_ETIMEOUT) on the current device; reading clears it.  Synchronises the
  * device. */
 int pt_device_status(void);
+
+/* Failure-path hook for the stream-K versions (a testing aid; the paper has
+ * no counterpart).  In a stream-K launch, the CTA that finishes a tile shared
+ * by several CTAs waits, with a time limit, for flags the others set when
+ * their partial tiles are written; a wait that runs out skips that tile's
+ * stores, sets the device error word (pt_device_status then returns
+ * PT_ETIMEOUT) and lets the kernel end normally.  This call sets, for the
+ * launches made after it in the process: the limit of that wait (limit_ns;
+ * 0 restores the default of 2 s, larger values are PT_EINVAL), and, with
+ * never_ready = 1, a flag value that no CTA writes, so every such wait runs
+ * out.  never_ready = 0 and limit_ns = 0 restore normal operation.  Only
+ * that inter-CTA wait is affected; the pipeline's own waits keep 2 s. */
+int pt_debug_streamk_wait(uint64_t limit_ns, int never_ready);
 
 /* Kernel timer (a measurement aid; the paper has no counterpart).  While it
  * runs on the calling host thread, every pt_sgemm / pt_sgemm_variant call

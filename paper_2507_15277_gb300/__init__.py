@@ -153,6 +153,11 @@ def shutdown() -> None:
     _lib.check(_l().pt_shutdown(), "pt_shutdown")
 
 
+def debug_streamk_wait(limit_ns: int = 0, never_ready: bool = False) -> None:
+    """Failure-path hook of the stream-K hand-over wait (see the header)."""
+    _lib.check(_l().pt_debug_streamk_wait(int(limit_ns), int(bool(never_ready))), "pt_debug_streamk_wait")
+
+
 def kernel_timer_start() -> None:
     """Starts timing the main GEMM kernel of every sgemm call on this thread."""
     _lib.check(_l().pt_kernel_timer_start(), "pt_kernel_timer_start")
@@ -179,9 +184,11 @@ def _shapes(shapes):
 
 def tune(shapes, table_path: str, ids=None, warmup: int = 2, reps_min: int = 5, reps_max: int = 50,
          target_ms: float = 5.0, seed: int = 1, resume: bool = False, tol: float = 2e-6,
-         pool_bytes: int = 1 << 30, verbose: bool = False) -> None:
-    """Timing table for ``shapes`` ((M, N, K[, transA, transB]) tuples) x variants."""
-    opts = TuneOpts(warmup, reps_min, reps_max, target_ms, seed, int(resume), tol, pool_bytes, int(verbose))
+         pool_bytes: int = 1 << 30, verbose: bool = False, fail_launch: int = 0) -> None:
+    """Timing table for ``shapes`` ((M, N, K[, transA, transB]) tuples) x variants.
+    ``fail_launch`` (testing): the n-th variant launch reports a failure."""
+    opts = TuneOpts(warmup, reps_min, reps_max, target_ms, seed, int(resume), tol, pool_bytes, int(verbose),
+                    int(fail_launch))
     arr = _shapes(shapes)
     if ids is None:
         idp, nid = None, 0

@@ -57,7 +57,8 @@ class Shape(ctypes.Structure):
 class TuneOpts(ctypes.Structure):
     _fields_ = [("warmup", ctypes.c_int), ("reps_min", ctypes.c_int), ("reps_max", ctypes.c_int),
                 ("target_ms", ctypes.c_double), ("seed", ctypes.c_uint64), ("resume", ctypes.c_int),
-                ("tol", ctypes.c_double), ("pool_bytes", _i64), ("verbose", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("pool_bytes", _i64), ("verbose", ctypes.c_int),
+                ("fail_launch", _i64)]
 
 
 class Problem(ctypes.Structure):
@@ -100,6 +101,7 @@ SIGNATURES = {
     "pt_kernel_timer_start": (ctypes.c_int, []),
     "pt_kernel_timer_stop": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "pt_sgemm_3xtf32_noalloc": (ctypes.c_int, _GEMM_ARGS),
+    "pt_debug_streamk_wait": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
     "pt_grouped_plan": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int]),
     "pt_sgemm_grouped": (ctypes.c_int, [ctypes.POINTER(Problem), _p, ctypes.c_int, _p]),
 }

@@ -105,7 +105,7 @@ int current_device() {
 // Error word written by kernels whose bounded waits gave up (one per device).
 __device__ int g_err_word;
 
-static int *err_word(int dev) {
+int *err_word(int dev) {
     static std::atomic<int *> ptrs[64];
     if (dev < 0 || dev >= 64) return nullptr;
     int *p = ptrs[dev].load(std::memory_order_acquire);
@@ -116,6 +116,15 @@ static int *err_word(int dev) {
         ptrs[dev].store(p, std::memory_order_release);
     }
     return p;
+}
+
+// Stream-K finisher wait (pt_debug_streamk_wait): limit and awaited-value offset.
+static std::atomic<uint64_t> g_sk_wait_ns{kWaitLimitNs};
+static std::atomic<unsigned> g_sk_wait_bias{0};
+
+void streamk_wait_settings(uint64_t *limit_ns, unsigned *bias) {
+    *limit_ns = g_sk_wait_ns.load(std::memory_order_relaxed);
+    *bias = g_sk_wait_bias.load(std::memory_order_relaxed);
 }
 
 // ---- small kernels -------------------------------------------------------------
@@ -330,6 +339,16 @@ int pt_sgemm_reference(char transA, char transB, int64_t M, int64_t N, int64_t K
     reference_kernel<<<grid, block, 0, st>>>(g);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PT_OK : set_error(PT_ECUDA, 0, "reference kernel: %s", cudaGetErrorString(e));
+}
+
+int pt_debug_streamk_wait(uint64_t limit_ns, int never_ready) {
+    clear_error();
+    if (limit_ns > kWaitLimitNs) return set_error(PT_EINVAL, 1, "limit above the default %llu ns",
+                                                  (unsigned long long)kWaitLimitNs);
+    if (never_ready != 0 && never_ready != 1) return set_error(PT_EINVAL, 2, "never_ready must be 0 or 1");
+    g_sk_wait_ns.store(limit_ns ? limit_ns : kWaitLimitNs, std::memory_order_relaxed);
+    g_sk_wait_bias.store((unsigned)never_ready, std::memory_order_relaxed);
+    return PT_OK;
 }
 
 int pt_kernel_timer_start(void) {

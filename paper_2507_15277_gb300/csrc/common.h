@@ -75,6 +75,7 @@ struct Manifest {
     // prediction at an unlisted shape adds the 1/d^2-weighted mean of the
     // member's residuals, d the L1 distance in (log2 M, log2 N, log2 K).
     std::vector<pt_shape_t> model_pts;
+    std::vector<double> model_pts_log2;  // (log2 M, log2 N, log2 K) of each point, 3 per point
     std::vector<std::vector<double>> resid;
     double train_geomean = 0;
 };

@@ -26,6 +26,16 @@ EncodeTiledFn encode_tiled_fn();
 // cudaSetDevice, so it is queried; the call is cheap).
 int current_device();
 
+// Device address of the library's error word on device `dev` (api.cu): kernels
+// whose bounded waits give up write PT_ETIMEOUT's cause there, and
+// pt_device_status reads and clears it.  A file-scope __device__ variable, so
+// looking it up allocates nothing; NULL if the lookup fails.
+int *err_word(int dev);
+
+// Stream-K finisher wait settings for the next launches (api.cu,
+// pt_debug_streamk_wait): time limit in ns and the awaited-value offset.
+void streamk_wait_settings(uint64_t *limit_ns, unsigned *bias);
+
 // Kernel timer (api.cu): records an event on `st` before (begin = true) or
 // after the main GEMM kernel of a call while pt_kernel_timer_start is active
 // on this host thread; otherwise does nothing.

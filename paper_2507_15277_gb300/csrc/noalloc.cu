@@ -17,10 +17,13 @@
 #include "launch.cuh"
 #include "tc.cuh"
 
-// Scratch for the split planes of both operands.  Every GPU that loads the
-// library holds these PT_NOALLOC_SCRATCH_BYTES bytes until the process exits.
-// In host code this name is only a stand-in for the device array: its device
-// address comes from cudaGetSymbolAddress below.
+// Scratch for the split planes of both operands.  Every GPU on which this
+// file's module is loaded holds these PT_NOALLOC_SCRATCH_BYTES bytes until the
+// process exits.  With CUDA's default lazy module loading that happens at the
+// first call on the device (the cudaGetSymbolAddress below loads the module);
+// with CUDA_MODULE_LOADING=EAGER, when the context is created.  In host code
+// this name is only a stand-in for the device array: its device address comes
+// from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char pt_noalloc_scratch[PT_NOALLOC_SCRATCH_BYTES];
 
 namespace pt {
@@ -29,24 +32,33 @@ namespace {
 using NoAllocCfg = Tc<kTcTf32, 128, 3>;
 
 std::atomic<unsigned char *> g_scratch_addr[64];
+std::atomic<int> g_sms[64];
 std::atomic<uint64_t> g_attr_done{0};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (with that device current) on the first call.
-int scratch_address(int dev, unsigned char **out) {
+// per device (with that device current) on the first call; the same call
+// caches the device's SM count (the persistent grid's size).
+int scratch_address(int dev, unsigned char **out, int *sms) {
     if (dev < 0 || dev >= 64) return set_error(PT_EUNSUPPORTED, 0, "device ordinal %d out of range", dev);
     unsigned char *p = g_scratch_addr[dev].load(std::memory_order_acquire);
     if (!p) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        g_sms[dev].store(n, std::memory_order_relaxed);
         void *q = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&q, pt_noalloc_scratch);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return set_error(PT_ECUDA, 0, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+            return set_error(PT_ECUDA, 0,
+                             "cudaGetSymbolAddress of the %u-byte scratch array (loading its module commits that "
+                             "device memory; is it free?): %s",
+                             (unsigned)PT_NOALLOC_SCRATCH_BYTES, cudaGetErrorString(e));
         }
         p = static_cast<unsigned char *>(q);
         g_scratch_addr[dev].store(p, std::memory_order_release);
     }
     *out = p;
+    *sms = g_sms[dev].load(std::memory_order_relaxed);
     return PT_OK;
 }
 
@@ -131,7 +143,8 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
 
     const int dev = current_device();
     unsigned char *ws = nullptr;
-    int rc = scratch_address(dev, &ws);
+    int sms = 1;
+    int rc = scratch_address(dev, &ws, &sms);
     if (rc != PT_OK) return rc;
     const uint64_t bit = 1ull << (dev & 63);
     if (!(g_attr_done.load(std::memory_order_acquire) & bit)) {
@@ -173,10 +186,16 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     t.alpha = alpha;
     t.beta = beta;
     t.vec4 = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
-    t.err = nullptr;
+    t.err = err_word(dev);  // a file-scope device word as well: no allocation
     t.sk_words = nullptr;  // no stream-K in this entry point
     t.sk_partials = nullptr;
-    const dim3 grid((unsigned)(((N + NoAllocCfg::BN - 1) / NoAllocCfg::BN) * ((M + NoAllocCfg::BM - 1) / NoAllocCfg::BM)));
+    t.sk_wait_ns = kWaitLimitNs;
+    t.sk_wait_bias = 0;
+    // Persistent grid: one CTA per SM walks the tiles (as the registry's
+    // tc3xtf32_m128n128_p3 does), so a CTA's producer runs ahead into its
+    // next tile while the epilogue drains the previous one.
+    const int64_t tiles = ((N + NoAllocCfg::BN - 1) / NoAllocCfg::BN) * ((M + NoAllocCfg::BM - 1) / NoAllocCfg::BM);
+    const dim3 grid((unsigned)(tiles < sms ? tiles : sms));
     tc_sgemm_kernel<NoAllocCfg><<<grid, NoAllocCfg::THREADS, NoAllocCfg::SMEM_BYTES, st>>>(t, mA, mB);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "tensor-core kernel: %s", cudaGetErrorString(e));

@@ -899,6 +899,9 @@ int read_manifest(const char *path, Manifest *out) {
                 sh.transA = m.model_ta;
                 sh.transB = m.model_tb;
                 m.model_pts.push_back(sh);
+                m.model_pts_log2.push_back(std::log2((double)sh.m));
+                m.model_pts_log2.push_back(std::log2((double)sh.n));
+                m.model_pts_log2.push_back(std::log2((double)sh.k));
             }
             for (size_t i = 0; i < rv->arr.size(); ++i) {
                 const json::Value &e = rv->arr[i];
@@ -947,6 +950,16 @@ int manifest_pick(const Manifest &m, const pt_shape_t &s) {
     if (!m.coef.empty() && s.transA == m.model_ta && s.transB == m.model_tb) {
         double f[kModelFeatures];
         model_features(s, f);
+        // Distances from the query to the model's points, once per pick: the
+        // same L1 distance in (log2 M, log2 N, log2 K) for every member.
+        const size_t np = m.model_pts.size();
+        std::vector<double> dist(np);
+        const double q[3] = {std::log2((double)s.m), std::log2((double)s.n), std::log2((double)s.k)};
+        const bool have_logs = m.model_pts_log2.size() == 3 * np;
+        for (size_t j = 0; j < np; ++j)
+            dist[j] = have_logs ? std::fabs(q[0] - m.model_pts_log2[3 * j]) + std::fabs(q[1] - m.model_pts_log2[3 * j + 1]) +
+                                      std::fabs(q[2] - m.model_pts_log2[3 * j + 2])
+                                : log_distance(s, m.model_pts[j]);
         int best = -1;
         double bp = kInf;
         for (size_t i = 0; i < m.kappa.size() && i < m.coef.size(); ++i) {
@@ -959,10 +972,10 @@ int manifest_pick(const Manifest &m, const pt_shape_t &s) {
                 // mean of those shapes' residuals (their measured ln t).
                 double num = 0, den = 0, at = 0;
                 int n_at = 0;
-                for (size_t j = 0; j < m.model_pts.size(); ++j) {
+                for (size_t j = 0; j < np; ++j) {
                     const double r = m.resid[i][j];
                     if (!std::isfinite(r)) continue;
-                    const double d = log_distance(s, m.model_pts[j]);
+                    const double d = dist[j];
                     if (d == 0.0) {
                         at += r;
                         ++n_at;

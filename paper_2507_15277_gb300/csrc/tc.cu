@@ -179,6 +179,7 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     t.err = a.err;
     t.sk_words = static_cast<unsigned *>(ws);
     t.sk_partials = reinterpret_cast<float *>(static_cast<unsigned char *>(ws) + header);
+    streamk_wait_settings(&t.sk_wait_ns, &t.sk_wait_bias);
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)grid, 1, V::SPLITK);

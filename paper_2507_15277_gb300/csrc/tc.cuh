@@ -206,6 +206,11 @@ struct TcArgs {
     // CTA b's partial tile (partials + b * BM * BN, row-major BM x BN).
     unsigned *sk_words;
     float *sk_partials;
+    // Stream-K finisher's wait for a contributor's flag: time limit (ns) and
+    // the offset of the awaited value from epoch + 1 (0; 1 only under the
+    // test hook pt_debug_streamk_wait, which makes the value one nobody writes).
+    uint64_t sk_wait_ns;
+    unsigned sk_wait_bias;
 };
 
 constexpr int kSkFlags = 32;                  // first flag word
@@ -632,8 +637,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     const unsigned *flag = args.sk_words + kSkFlags + 4 * j + warp;
                     const uint64_t t0 = globaltimer_ns();
                     bool ready = false;
-                    while (!(ready = ld_acquire_u32(flag) == epoch1)) {
-                        if (globaltimer_ns() - t0 > kWaitLimitNs) break;
+                    while (!(ready = ld_acquire_u32(flag) == epoch1 + args.sk_wait_bias)) {
+                        if (globaltimer_ns() - t0 > args.sk_wait_ns) break;
                     }
                     if (!__all_sync(0xffffffffu, ready)) {
                         epi_ok = false;

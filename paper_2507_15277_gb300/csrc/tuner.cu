@@ -119,6 +119,7 @@ void pt_tune_default_opts(pt_tune_opts_t *o) {
     o->tol = 2e-6;
     o->pool_bytes = (int64_t)1 << 30;
     o->verbose = 0;
+    o->fail_launch = 0;
 }
 
 int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids, const pt_tune_opts_t *opts_in,
@@ -130,7 +131,8 @@ int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids, c
     pt_tune_opts_t o;
     pt_tune_default_opts(&o);
     if (opts_in) o = *opts_in;
-    if (o.warmup < 0 || o.reps_min < 1 || o.reps_max < o.reps_min || !(o.target_ms > 0) || !(o.tol > 0))
+    if (o.warmup < 0 || o.reps_min < 1 || o.reps_max < o.reps_min || !(o.target_ms > 0) || !(o.tol > 0) ||
+        o.fail_launch < 0)
         return set_error(PT_EINVAL, 5, "invalid tuning options");
     std::vector<int> vids;
     if (ids) {
@@ -186,6 +188,12 @@ int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids, c
     for (size_t i = 0; ce == cudaSuccess && i < ev.size(); ++i) ce = cudaEventCreate(&ev[i]);
     if (ce == cudaSuccess) ce = cudaMalloc(&buf.cmp, sizeof(CmpOut));
     if (ce != cudaSuccess) rc = cuda_fail(ce, "tuner setup");
+    int64_t launches = 0;  // variant launches made (the fail_launch hook counts them)
+    auto run = [&](const VariantEntry &ve, const GemmArgs &g) {
+        if (++launches == o.fail_launch) return set_error(PT_ECUDA, 0, "launch %lld failed (injected)",
+                                                          (long long)launches);
+        return ve.launch(g, st, false);
+    };
 
     for (int s = 0; rc == PT_OK && s < n_shapes; ++s) {
         const pt_shape_t &sh = shapes[s];
@@ -266,7 +274,7 @@ int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids, c
             if (lr == PT_OK) {
                 // Screening run on replica 0 with C poisoned (all-ones bits = NaN).
                 cudaMemsetAsync(C_of(0), 0xFF, (size_t)M * N * 4, st);
-                lr = ve.launch(g, st, false);
+                lr = run(ve, g);
                 if (lr == PT_OK) {
                     cudaMemcpyAsync(buf.cmp, &zero, sizeof(zero), cudaMemcpyHostToDevice, st);
                     compare_kernel<<<1024, 256, 0, st>>>(C_of(0), ldc, buf.ref, ldc, M, N, buf.cmp);
@@ -293,7 +301,7 @@ int pt_tune(const pt_shape_t *shapes, int n_shapes, const int *ids, int n_ids, c
                     GemmArgs h = g;
                     const int idx = r++ % nrep;
                     h.A = A_of(idx); h.B = B_of(idx); h.C = C_of(idx);
-                    return ve.launch(h, st, false);
+                    return run(ve, h);
                 };
                 int e2 = PT_OK;
                 for (int w = 0; w < o.warmup && e2 == PT_OK; ++w) e2 = launch_rep();

@@ -47,3 +47,33 @@ def test_traffic_records_are_well_formed():
         got = bench.traffic_for(e["kernel"], tuple(e["shape"]))
         assert got == (e["dram_bytes"] if current else None)
     assert bench.traffic_for("no_such_kernel", (1, 1, 1)) is None
+
+
+def test_selection_by_kind_on_a_synthetic_table(tmp_path):
+    # Three variants of each kind on 8 shapes; the family's per-shape best is
+    # a BF16x3 variant on the large shapes and a SIMT one on the small ones.
+    pt = pytest.importorskip("paper_2507_15277_gb300")
+    vs = pt.variants()
+    by_kind = {k: [v["name"] for v in vs if v["kind"] == k][:3] for k in (0, 1, 2)}
+    shapes = [(m, n, k) for m in (128, 4096) for n in (128, 4096) for k in (128, 4096)]
+    rng = np.random.default_rng(0)
+    path = str(tmp_path / "table.csv")
+    with open(path, "w") as f:
+        f.write("shape_idx,M,N,K,transA,transB,variant,status,valid,median_ms,mean_ms,min_ms,reps,tflops,gbs,max_err\n")
+        for s, (m, n, k) in enumerate(shapes):
+            big = m * n * k > 128 ** 3 * 64
+            for kind, names in by_kind.items():
+                for j, name in enumerate(names):
+                    t = (1.0 + 0.3 * j + 0.1 * rng.random()) * (2.0 if (kind == 0) == big else 1.0)
+                    f.write("%d,%d,%d,%d,N,N,%s,0,1,%.6f,%.6f,%.6f,5,1,1,0\n" % (s, m, n, k, name, t, t, t))
+    train, held = list(range(0, 8, 2)), list(range(1, 8, 2))
+    res = bench.selection_by_kind(pt, path, train, held, str(tmp_path))
+    assert set(res) == {"fp32_simt", "3xtf32", "bf16x3"}
+    for label, r in res.items():
+        assert r["variants"] == 3
+        for k in ("k1", "k2", "k4", "k8"):
+            own, fam = r[k]["own_best_pct"], r[k]["family_best_pct"]
+            assert 0 < fam <= own <= 100 + 1e-9        # the family's best is at least as fast
+        assert r["k4"]["own_best_pct"] == pytest.approx(100.0)   # every variant of the kind chosen
+    # neither single kind reaches the family's best on every held-out shape
+    assert all(r["k8"]["family_best_pct"] < 100.0 for r in res.values())

@@ -98,6 +98,22 @@ def test_argument_validation_without_gpu():
     assert lib.pt_variant_by_name(b"no_such_variant") == _lib.PT_EINVAL
 
 
+def test_failure_hooks_arguments_without_gpu():
+    lib = _lib.lib()
+    o = _lib.TuneOpts()
+    o.fail_launch = 77
+    lib.pt_tune_default_opts(o)
+    assert o.fail_launch == 0 and o.warmup == 2 and o.tol == 2e-6
+    assert lib.pt_debug_streamk_wait(3 * 10 ** 9, 0) == _lib.PT_EINVAL and lib.pt_last_error_arg() == 1
+    assert lib.pt_debug_streamk_wait(1000, 2) == _lib.PT_EINVAL and lib.pt_last_error_arg() == 2
+    assert lib.pt_debug_streamk_wait(1000, 1) == 0
+    assert lib.pt_debug_streamk_wait(0, 0) == 0      # back to normal operation
+    # a negative launch index is refused before any device work
+    o.fail_launch = -1
+    shapes = (_lib.Shape * 1)(_lib.Shape(8, 8, 8, b"N", b"N"))
+    assert lib.pt_tune(shapes, 1, None, 0, o, b"/nonexistent/t.csv") == _lib.PT_EINVAL
+
+
 # ---- selection against the oracle ------------------------------------------------------
 
 HEADER_CSV = "shape_idx,M,N,K,transA,transB,variant,status,valid,median_ms,mean_ms,min_ms,reps,tflops,gbs,max_err"

@@ -13,6 +13,8 @@ from .rng import (  # noqa: F401
     normal,
     log_uniform_signed,
     matrix,
+    rank1_operands,
+    wide_int_operands,
 )
 from .shapes import (  # noqa: F401
     SWEEP_SIZES,

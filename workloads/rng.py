@@ -120,3 +120,54 @@ def matrix(kind: str, seed: int, rows: int, cols: int, ld: int | None = None, **
     out = np.full((rows, ld), np.nan, dtype=np.float32)
     out[:, :cols] = vals
     return out
+
+
+def rank1_operands(M: int, N: int, K: int):
+    """A (M x K) of ones and B (K x N) with B[k][j] = k: every entry of A*B is
+    sum_{k<K} k = K(K-1)/2, a closed form (exact in FP32 for K <= 4096)."""
+    A = np.ones((M, K), np.float32)
+    B = np.repeat(np.arange(K, dtype=np.float32)[:, None], N, axis=1)
+    return A, np.ascontiguousarray(B)
+
+
+def _signed_ints(seed: int, n: int, lo: int, hi: int, odd: bool = False) -> np.ndarray:
+    """n FP64 integers of magnitude uniform on [lo, hi) (odd ones only when
+    ``odd``) with a random sign."""
+    x = _bits(seed, n)
+    if odd:
+        mag = ((x >> np.uint64(33)) % np.uint64((hi - lo) // 2)) * np.uint64(2) + np.uint64(lo + 1)
+    else:
+        mag = (x >> np.uint64(33)) % np.uint64(hi - lo) + np.uint64(lo)
+    sign = np.where((x & np.uint64(1)) == 1, -1.0, 1.0)
+    return sign * mag.astype(np.float64)
+
+
+def wide_int_operands(seed: int, M: int, N: int, K: int):
+    """Integer operands with 18-, 9- and 1-bit entries whose exact product
+    stays below 2^24 in every partial sum.
+
+    Each k has a type t = k mod 3:
+      t = 0: A[i][k] has magnitude in [2^17, 2^18) (18 bits), B[k][j] is +-1;
+      t = 1: A[i][k] is +-1, B[k][j] has magnitude in [2^17, 2^18);
+      t = 2: both are odd with magnitude in [2^8, 2^9) (9 bits).
+    B is dense.  A[i][k] is non-zero only where (k - i) mod P is 0, 1 or 2,
+    with P = max(64, ceil(K / 16)): row i meets at most 16 windows of three
+    consecutive k (one of each type), so sum_k |A[i][k] B[k][j]| is below
+    16 * 3 * 2^18 < 2^24, and every row offset of A touches a different k,
+    so with M >= P every k of every operand is used.
+    Returns (A, B, P).
+    """
+    P = max(64, -(-K // 16))
+    t = np.arange(K) % 3
+    big = _signed_ints(seed, M * K, 1 << 17, 1 << 18).reshape(M, K)
+    mid = _signed_ints(seed + 1, M * K, 1 << 8, 1 << 9, odd=True).reshape(M, K)
+    one = _signed_ints(seed + 2, M * K, 1, 2).reshape(M, K)
+    A = np.where(t == 0, big, np.where(t == 1, one, mid))
+    window = (np.arange(K)[None, :] - np.arange(M)[:, None]) % P < 3
+    A = np.where(window, A, 0.0)
+    bbig = _signed_ints(seed + 3, K * N, 1 << 17, 1 << 18).reshape(K, N)
+    bmid = _signed_ints(seed + 4, K * N, 1 << 8, 1 << 9, odd=True).reshape(K, N)
+    bone = _signed_ints(seed + 5, K * N, 1, 2).reshape(K, N)
+    tk = t[:, None]
+    B = np.where(tk == 0, bone, np.where(tk == 1, bbig, bmid))
+    return np.ascontiguousarray(A.astype(np.float32)), np.ascontiguousarray(B.astype(np.float32)), P
