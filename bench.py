@@ -181,7 +181,7 @@ def report_splitprec(args):
         Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
         ref = pt.reference(Ad, Bd)[sample].cpu().numpy().astype(np.float64)
         entry = {"shape": [M, N, K]}
-        for kind, label in ((0, "fp32_simt"), (1, "3xtf32"), (2, "bf16x3")):
+        for kind, label in KIND_LABELS.items():
             if kind not in best:
                 continue
             t, name = best[kind]
@@ -651,7 +651,10 @@ def cpu_oracle_sample(shapes, rows_per_shape, seed_base=1000):
     return flops / dt / 1e12, dt, og.num_threads(), flops
 
 
-KIND_LABELS = {0: "fp32_simt", 1: "3xtf32", 2: "bf16x3"}
+KIND_LABELS = {0: "fp32_simt", 1: "3xtf32", 2: "bf16x3", 3: "3xf16"}
+# Tensor-core kinds: (MMA products per FP32 product, MMA input type, its
+# dense rate relative to BF16).
+TC_KINDS = {1: (3, "tf32", 1.1 / 2.25), 2: (6, "bf16", 1.0), 3: (3, "f16", 1.0)}
 
 
 def selection_by_kind(pt, table, train, held, out_dir):
@@ -1067,7 +1070,7 @@ def main():
     else:
         # Split-precision tensor-core kernel: the tensor pipe executes
         # (products per FP32 product) x 2MNK flops of TF32 or BF16 MMAs.
-        nprod, ratio, dt = (3, 1.1 / 2.25, "tf32") if dvar["kind"] == 1 else (6, 1.0, "bf16")
+        nprod, dt, ratio = TC_KINDS[dvar["kind"]]
         achieved = nprod * flops[dom] / (dom_ms * 1e-3) / 1e12
         bf16 = peaks.get("bf16_tflops") or 1900.0
         bf16_sus = peaks.get("bf16_tflops_sustained") or 1700.0
@@ -1105,7 +1108,7 @@ def main():
         kind = pt.variant(p)["kind"]
         d = {"frac_fp32_peak": round(tf / fp32_peak, 4)}
         if kind:
-            nprod, ratio = (3, 1.1 / 2.25) if kind == 1 else (6, 1.0)
+            nprod, _, ratio = TC_KINDS[kind]
             d["frac_tensor_peak"] = round(nprod * tf / (bf16_peak * ratio), 4)
         return d
 

@@ -113,7 +113,9 @@ typedef struct pt_variant_desc {
     int trans_mask;    /* bit (2*tA + tB) set when (transA, transB) runs;
                           tX = 0 for 'N', 1 for 'T'                          */
     int kind;          /* 0 = FP32 SIMT, 1 = 3xTF32 tensor core (tcgen05),
-                          2 = BF16x3 tensor core (tcgen05, six products)     */
+                          2 = BF16x3 tensor core (tcgen05, six products),
+                          3 = scaled 3xF16 tensor core (tcgen05, three FP16
+                          products, per-chunk power-of-two scales)         */
     int fma2;          /* 1: packed fma.rn.f32x2 register-tile updates       */
     int schedule;      /* PT_SCHED_*                                         */
     char name[96];     /* stable key used in tables and manifests           */
@@ -123,16 +125,23 @@ int pt_num_variants(void);
 int pt_variant_desc(int id, pt_variant_desc_t *out);
 /* id of a variant by name, or PT_EINVAL */
 int pt_variant_by_name(const char *name);
-/* The split-precision tensor-core variants (kind 1, 2) split both operands
+/* The split-precision tensor-core variants (kind 1, 2, 3) split both operands
  * into low-precision planes in a library workspace (see pt_shutdown) and run
  * tcgen05.mma with TMEM accumulators; they accept every layout and alignment.
  * Exception: fused versions (names with "_fa" / "_fb") split A (or B) inside
  * the GEMM kernel from the caller's matrix, so they need that operand
  * untransposed (trans_mask), 16-byte aligned, with a leading dimension
  * divisible by 4, and return PT_EUNSUPPORTED otherwise.
- * 3xTF32 (Markidis et al.-style split x = hi + lo, three products) and BF16x3
- * (x = b0 + b1 + b2, six products) give FP32-level error.  The paper has no
- * tensor-core versions; they are further members of the same variant space. */
+ * 3xTF32 (Markidis et al.-style split x = hi + lo, three products), BF16x3
+ * (x = b0 + b1 + b2, six products) and scaled 3xF16 give FP32-level error.
+ * 3xF16 ("tc3xf16_" names) multiplies each row of op(A) and each column of
+ * op(B), per 128 values of k, by a power of two that brings the largest
+ * magnitude there into [2^14, 2^15), splits into two FP16 planes (11-bit
+ * significands, as TF32) and undoes the scales on each 128-k partial product:
+ * three MMAs at the FP16 rate.  It gives that accuracy while those chunk
+ * maxima lie in [2^-49, 2^78]; larger values overflow FP16 (C gets Inf or
+ * NaN) and smaller ones keep fewer bits.  The paper has no tensor-core
+ * versions; they are further members of the same variant space. */
 /* the fixed default variant (128x128x8 CTA tile, cp.async, any layout) */
 int pt_default_variant(void);
 

@@ -10,8 +10,17 @@ planes and drop the smallest cross products:
           b2 = RN_bf16(x - b0 - b1);
           a*b ~ sum of a_i*b_j over i + j <= 2       (a1b2, a2b1, a2b2 dropped)
 
+  3xF16 (scaled): each row of op(A) and each column of op(B) is cut into
+          chunks of 128 values of k; a chunk is multiplied by 2^S with
+          S = 14 - floor(log2 m), m its largest magnitude, clamped to
+          [-63, 63] (63 when m = 0); then x' = h0 + h1 with h0 = RN_f16(x'),
+          h1 = RN_f16(x' - h0) and the products kept as in 3xTF32; each
+          chunk's sum is multiplied back by 2^-S_A 2^-S_B.
+
 RN_p rounds to the nearest value with p significant bits, ties to even
-(TF32: p = 11, BF16: p = 8; the FP32 exponent range is kept).  This module
+(TF32: p = 11, BF16: p = 8; the FP32 exponent range is kept).  RN_f16 is
+IEEE binary16 rounding (11 significant bits, subnormals below 2^-14),
+taken from numpy's float16 conversion.  This module
 states the rounding arithmetically (frexp / ldexp and numpy's round-half-even)
 so that tests can show which planes and which products a set of inputs
 exercises.  Only the tests use it; the library splits with bit operations of
@@ -49,6 +58,34 @@ def bf16x3_planes(x):
     b1 = round_sig(x - b0, P_BF16)
     b2 = round_sig(x - b0 - b1, P_BF16)
     return b0, b1, b2
+
+
+def f16_chunk_scales(X, chunk: int = 128) -> np.ndarray:
+    """Exponents S[r, c] of the 3xF16 split of the rows of X (rows x K):
+    2^S brings the largest magnitude of chunk c of row r into [2^14, 2^15)."""
+    X = np.abs(np.asarray(X, dtype=np.float64))
+    rows, K = X.shape
+    nch = -(-K // chunk)
+    S = np.empty((rows, nch), dtype=np.int64)
+    for c in range(nch):
+        m = X[:, c * chunk:(c + 1) * chunk].max(axis=1) if K else np.zeros(rows)
+        with np.errstate(divide="ignore"):
+            e = np.where(m > 0, np.floor(np.log2(np.where(m > 0, m, 1.0))), -1000)
+        S[:, c] = np.clip(14 - e, -63, 63).astype(np.int64)
+    return S
+
+
+def f16x2_planes_scaled(X, chunk: int = 128):
+    """(h0, h1, S) of the scaled 3xF16 split of the rows of X: h0 + h1 is
+    X[r, k] * 2^S[r, k // chunk] on the FP16 grid (FP64 arrays)."""
+    X = np.asarray(X, dtype=np.float64)
+    S = f16_chunk_scales(X, chunk)
+    scale = np.ldexp(1.0, np.repeat(S, chunk, axis=1)[:, :X.shape[1]])
+    xs = X * scale
+    with np.errstate(over="ignore", invalid="ignore"):   # beyond FP16's range: inf, as the kernel
+        h0 = xs.astype(np.float16).astype(np.float64)
+        h1 = (xs - h0).astype(np.float16).astype(np.float64)
+    return h0, h1, S
 
 
 BF16X3_KEPT = [(0, 0), (0, 1), (1, 0), (1, 1), (0, 2), (2, 0)]

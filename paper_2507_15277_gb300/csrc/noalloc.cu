@@ -191,6 +191,9 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     t.sk_partials = nullptr;
     t.sk_wait_ns = kWaitLimitNs;
     t.sk_wait_bias = 0;
+    t.scale_a = nullptr;  // 3xTF32: no scales
+    t.scale_b = nullptr;
+    t.ld_sa = t.ld_sb = 0;
     // Persistent grid: one CTA per SM walks the tiles (as the registry's
     // tc3xtf32_m128n128_p3 does), so a CTA's producer runs ahead into its
     // next tile while the epilogue drains the previous one.

@@ -1,6 +1,7 @@
 // Split kernel of the tensor-core versions: FP32 operands to K-major
-// low-precision planes (3xTF32: hi, lo; BF16x3: b0, b1, b2) in a workspace
-// that the GEMM kernel reads through TMA.
+// low-precision planes (3xTF32: hi, lo; BF16x3: b0, b1, b2; scaled 3xF16:
+// h0, h1 of the value times a power-of-two scale per row and 128 values of k)
+// in a workspace that the GEMM kernel reads through TMA.
 #pragma once
 
 #include <cstdint>
@@ -12,6 +13,43 @@ namespace pt {
 
 constexpr int kTcTf32 = 0;
 constexpr int kTcBf16x3 = 1;
+constexpr int kTcF16s = 2;  // scaled FP16 split, three products (3xTF32's precision, FP16 rate)
+
+// Scaled FP16 split: every row of an operand is cut into chunks of 128
+// values of k; chunk c of row r is multiplied by s = 2^S(r, c) before the
+// split, with S = 14 - floor(log2 m), m = max |x| over the chunk, clamped to
+// [-63, 63] (S = 63 when m = 0), so the chunk's largest magnitude lands in
+// [2^14, 2^15) (FP16 holds up to 65504).  The GEMM multiplies the chunk's
+// product by 2^-S_A(row, c) * 2^-S_B(col, c), a power of two in
+// [2^-126, 2^126], exactly representable.  Chunk maxima in [2^-49, 2^78]
+// get the full scale; beyond 2^78 the planes overflow to infinity, below
+// 2^-49 the values keep fewer bits (as FP32 products of such values do).
+constexpr int kF16ScaleMin = -63, kF16ScaleMax = 63;
+__device__ __forceinline__ int f16_scale_exp(float m) {
+    const int e = (int)((__float_as_uint(m) >> 23) & 0xffu);  // biased exponent of m (0: zero or subnormal)
+    int S = 141 - e;                                           // 14 - (e - 127)
+    S = S < kF16ScaleMin ? kF16ScaleMin : S;
+    return S > kF16ScaleMax ? kF16ScaleMax : S;
+}
+__device__ __forceinline__ float pow2f(int S) { return __uint_as_float((uint32_t)(S + 127) << 23); }
+
+// Two floats to FP16 with round-to-nearest-even (one cvt.rn.f16x2.f32): x0 in
+// the low half, x1 in the high half; and back to FP32 (exact).
+__device__ __forceinline__ uint32_t f16x2_rn(float x0, float x1) {
+    uint32_t d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(x1), "f"(x0));
+    return d;
+}
+__device__ __forceinline__ float f16_lo_f32(uint32_t p) {
+    float f;
+    asm("{\n .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %1;\n cvt.f32.f16 %0, lo;\n}" : "=f"(f) : "r"(p));
+    return f;
+}
+__device__ __forceinline__ float f16_hi_f32(uint32_t p) {
+    float f;
+    asm("{\n .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %1;\n cvt.f32.f16 %0, hi;\n}" : "=f"(f) : "r"(p));
+    return f;
+}
 
 // ---- splitting --------------------------------------------------------------------
 // Round to nearest even on the TF32 grid (10 explicit mantissa bits) by bit
@@ -53,6 +91,20 @@ __device__ __forceinline__ void split_store8(unsigned char *ws, int64_t plane_by
         ph[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
         pl[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
         pl[1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
+    } else if constexpr (KIND == kTcF16s) {
+        // h0 = RN(x), h1 = RN(x - h0) on the FP16 grid (x already scaled);
+        // the residual is exact in FP32.
+        uint32_t h[2][4];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            const uint32_t q = f16x2_rn(x[i], x[i + 1]);
+            h[0][i / 2] = q;
+            h[1][i / 2] = f16x2_rn(x[i] - f16_lo_f32(q), x[i + 1] - f16_hi_f32(q));
+        }
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl)
+            *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(ws + pl * plane_bytes) + off) =
+                make_uint4(h[pl][0], h[pl][1], h[pl][2], h[pl][3]);
     } else {
         // b0 = RN(x), b1 = RN(x - b0), b2 = RN(x - b0 - b1); the residuals
         // are exact in FP32.
@@ -93,6 +145,9 @@ struct SplitOperand {
     unsigned char *ws;
     int64_t plane_bytes;
     int vec4;  // src and ld allow 16-byte loads
+    // Scaled FP16 split only: 2^-S of row r, chunk c at scale[c * ld_scale + r].
+    float *scale = nullptr;
+    int64_t ld_scale = 0;
 };
 
 // Both operands in one launch: blocks with blockIdx.y < ya split `a`, the
@@ -164,6 +219,30 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, con
 #pragma unroll
                 for (int i = 0; i < 8; ++i) x[t][i] = (r < rows && k + i < K) ? p[i] : 0.f;
             }
+        }
+    }
+    if constexpr (KIND == kTcF16s) {
+        // Chunk scales: slabs 2c and 2c + 1 form chunk kb / 128 + c; the eight
+        // threads of a row (consecutive lanes) combine their maxima.
+        static_assert(SPLIT_KT % 2 == 0, "a block covers whole 128-k chunks");
+#pragma unroll
+        for (int c = 0; c < SPLIT_KT / 2; ++c) {
+            float m = 0.f;
+#pragma unroll
+            for (int t = 2 * c; t < 2 * c + 2; ++t)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) m = fmaxf(m, fabsf(x[t][i]));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+            const int S = f16_scale_exp(m);
+            const float s = pow2f(S);
+#pragma unroll
+            for (int t = 2 * c; t < 2 * c + 2; ++t)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) x[t][i] *= s;
+            const int gc = kb / 128 + c;
+            if ((tid & 7) == 0 && r < rows && 128 * gc < pitch) o.scale[(int64_t)gc * o.ld_scale + r] = pow2f(-S);
         }
     }
 #pragma unroll

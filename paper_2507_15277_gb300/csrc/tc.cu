@@ -113,10 +113,16 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
             grid = sms;
         }
     }
-    // Workspace: stream-K header, stream-K partial tiles, then the planes.
+    // Workspace: stream-K header, stream-K partial tiles, the planes, then
+    // (3xF16) the chunk scales of A and B, [chunk][row] with padded rows.
     const int64_t header = align256((int64_t)kSkHeaderBytes);
     const int64_t partials = V::STREAMK ? align256(grid * V::BM * V::BN * 4) : 0;
-    const size_t need = (size_t)(header + partials) + (size_t)V::P * (size_t)(a_plane + b_plane);
+    const int64_t nchk = ((int64_t)a.K + 127) / 128;
+    const int64_t ld_sa = ((int64_t)a.M + 127) / 128 * 128, ld_sb = ((int64_t)a.N + 127) / 128 * 128;
+    const int64_t sa_bytes = V::SCALED ? align256(nchk * ld_sa * 4) : 0;
+    const int64_t sb_bytes = V::SCALED ? align256(nchk * ld_sb * 4) : 0;
+    const size_t need =
+        (size_t)(header + partials) + (size_t)V::P * (size_t)(a_plane + b_plane) + (size_t)(sa_bytes + sb_bytes);
     void *ws = nullptr;
     int rc = workspace(st, need, dry, &ws);
     if (rc != PT_OK || dry) return rc;
@@ -132,10 +138,12 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
 
     unsigned char *wA = static_cast<unsigned char *>(ws) + header + partials;
     unsigned char *wB = wA + V::P * a_plane;
+    float *scA = reinterpret_cast<float *>(wB + V::P * b_plane);
+    float *scB = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(scA) + sa_bytes);
     const int va = (!misaligned(a.A, 16) && a.lda % 4 == 0) ? 1 : 0;
     const int vb = (!misaligned(a.B, 16) && a.ldb % 4 == 0) ? 1 : 0;
-    const SplitOperand oa{a.A, a.lda, a.ta, a.M, wA, a_plane, va};
-    const SplitOperand ob{a.B, a.ldb, a.tb ? 0 : 1, a.N, wB, b_plane, vb};
+    const SplitOperand oa{a.A, a.lda, a.ta, a.M, wA, a_plane, va, V::SCALED ? scA : nullptr, ld_sa};
+    const SplitOperand ob{a.B, a.ldb, a.tb ? 0 : 1, a.N, wB, b_plane, vb, V::SCALED ? scB : nullptr, ld_sb};
     // Blocks with blockIdx.y < ya split the first operand, the rest the second.
     const int ya = V::FUSEA ? (a.N + 31) / 32 : (a.M + 31) / 32;
     const int yb = V::FUSE ? 0 : (a.N + 31) / 32;
@@ -153,8 +161,9 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
                              : cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, oa, ob, (int)a.K, pitch, ya);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 
-    const CUtensorMapDataType dt =
-        V::KIND == kTcTf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapDataType dt = V::KIND == kTcTf32     ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : V::KIND == kTcBf16x3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     CUtensorMap mA, mB;
     if (V::FUSEA)
         rc = make_map_2d(&mA, a.A, a.K, a.M, a.lda, V::BK, V::BM, CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -180,6 +189,10 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     t.sk_words = static_cast<unsigned *>(ws);
     t.sk_partials = reinterpret_cast<float *>(static_cast<unsigned char *>(ws) + header);
     streamk_wait_settings(&t.sk_wait_ns, &t.sk_wait_bias);
+    t.scale_a = V::SCALED ? scA : nullptr;
+    t.scale_b = V::SCALED ? scB : nullptr;
+    t.ld_sa = ld_sa;
+    t.ld_sb = ld_sb;
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)grid, 1, V::SPLITK);
@@ -221,7 +234,7 @@ VariantEntry tc_entry(const char *name) {
     v.desc.threads = V::THREADS;
     v.desc.smem_bytes = V::SMEM_BYTES;
     v.desc.trans_mask = V::FUSEB ? 5 : (V::FUSEA ? 3 : 15);  // fused B: transB = N only; fused A: transA = N only
-    v.desc.kind = V::KIND == kTcTf32 ? 1 : 2;
+    v.desc.kind = V::KIND == kTcTf32 ? 1 : (V::KIND == kTcBf16x3 ? 2 : 3);
     v.desc.schedule = V::STREAMK ? PT_SCHED_STREAMK : (V::SPLITK > 1 ? PT_SCHED_TILE : PT_SCHED_PERSISTENT);
     std::strncpy(v.desc.name, name, sizeof(v.desc.name) - 1);
     v.launch = launch_tc<V>;
@@ -307,6 +320,22 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcBf16x3, 64, 4, 4, 64>>("tcbf16x3_m128n64_p4_sw64_sk4"),
         tc_entry<Tc<kTcBf16x3, 64, 4, 8, 64>>("tcbf16x3_m128n64_p4_sw64_sk8"),
         tc_entry<Tc<kTcBf16x3, 64, 4, 1, 64, 1>>("tcbf16x3_m128n64_p4_sw64_stk"),
+        // Scaled 3xF16: 3xTF32's 22 significand bits in three MMAs at the
+        // FP16 rate (half the tensor work of BF16x3, 4 bytes per element
+        // of planes instead of 6).
+        tc_entry<Tc<kTcF16s, 128, 3>>("tc3xf16_m128n128_p3"),
+        tc_entry<Tc<kTcF16s, 128, 6, 1, 64>>("tc3xf16_m128n128_p6_sw64"),
+        tc_entry<Tc<kTcF16s, 128, 3, 1, 128, 1>>("tc3xf16_m128n128_p3_stk"),
+        tc_entry<Tc<kTcF16s, 128, 6, 1, 64, 1>>("tc3xf16_m128n128_p6_sw64_stk"),
+        tc_entry<Tc<kTcF16s, 64, 4>>("tc3xf16_m128n64_p4"),
+        tc_entry<Tc<kTcF16s, 64, 4, 1, 128, 1>>("tc3xf16_m128n64_p4_stk"),
+        tc_entry<Tc<kTcF16s, 128, 3, 2>>("tc3xf16_m128n128_p3_sk2"),
+        tc_entry<Tc<kTcF16s, 128, 3, 4>>("tc3xf16_m128n128_p3_sk4"),
+        tc_entry<Tc<kTcF16s, 64, 4, 2>>("tc3xf16_m128n64_p4_sk2"),
+        tc_entry<Tc<kTcF16s, 64, 4, 4>>("tc3xf16_m128n64_p4_sk4"),
+        tc_entry<Tc<kTcF16s, 64, 4, 8>>("tc3xf16_m128n64_p4_sk8"),
+        tc_entry<Tc<kTcF16s, 32, 5, 4>>("tc3xf16_m128n32_p5_sk4"),
+        tc_entry<Tc<kTcF16s, 32, 5, 8>>("tc3xf16_m128n32_p5_sk8"),
     };
 }
 

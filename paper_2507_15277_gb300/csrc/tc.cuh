@@ -8,9 +8,15 @@
 //   BF16x3:  x = b0 + b1 + b2, b0 = RN_bf16(x), b1 = RN_bf16(x - b0),
 //            b2 = RN_bf16(x - b0 - b1);
 //            a*b ~ sum of the six b_i*b_j with i + j <= 2 (kind::f16 with BF16, 6 MMAs)
-// The dropped terms are O(2^-22) (3xTF32) and O(2^-24) (BF16x3) relative to
-// |a*b|, so the result is FP32-accurate; these variants join the FP32 SIMT
-// family as further versions of the same operation.
+//   3xF16:   x' = x * 2^S (S per row and 128 values of k, so that the chunk's
+//            largest |x'| is in [2^14, 2^15)), x' = h0 + h1 on the FP16 grid
+//            (11-bit significands, as TF32); a'*b' ~ h0 h0 + h0 h1 + h1 h0
+//            (kind::f16 with F16, 3 MMAs at the BF16 rate); each chunk's
+//            product is multiplied by 2^-S_A * 2^-S_B when it is drained.
+// The dropped terms are O(2^-22) (3xTF32, 3xF16) and O(2^-24) (BF16x3)
+// relative to |a*b| (3xF16: relative to the chunk's largest |a| |b|), so the
+// result is FP32-accurate; these variants join the FP32 SIMT family as
+// further versions of the same operation.
 //
 // Pipeline (a persistent CTA per SM walks the 128 x BN output tiles;
 // stream-K versions share the last waves' tiles in 128-k chunks; split-K
@@ -71,7 +77,7 @@ struct Tc {
     // M x K, K contiguous; pays for small N).
     static constexpr int FUSE = FUSE_;
     static constexpr bool FUSEB = FUSE == 1, FUSEA = FUSE == 2;
-    static_assert(FUSE == 0 || KIND_ == 1, "fused split is BF16x3 only");
+    static_assert(FUSE == 0 || KIND_ == kTcBf16x3, "fused split is BF16x3 only");
     // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
     // A narrower row makes the stage smaller, so more stages fit and the
     // producer refills a smaller part of the pipeline at a time.
@@ -81,13 +87,14 @@ struct Tc {
     // FP32 partial tiles are summed through distributed shared memory in
     // cluster-rank order (the pipeline's shared memory is reused for them).
     static constexpr int RED_LD = BN + 4;
+    static constexpr bool SCALED = KIND == kTcF16s;       // per-chunk scales applied when draining
     static constexpr int ELEM = KIND == kTcTf32 ? 4 : 2;  // bytes per plane element
-    static constexpr int P = KIND == kTcTf32 ? 2 : 3;     // planes per operand
+    static constexpr int P = KIND == kTcBf16x3 ? 3 : 2;   // planes per operand
     static constexpr int BK = SWZ / ELEM;                 // one swizzle row per tile row
     static constexpr int KSTEP = 32 / ELEM;               // K of one MMA instruction (32 bytes)
-    static constexpr int NPROD = KIND == kTcTf32 ? 3 : 6;
+    static constexpr int NPROD = KIND == kTcBf16x3 ? 6 : 3;
     // MMA instructions per k step after pairing along N (see tc_op).
-    static constexpr int NOPS = KIND == kTcTf32 ? 2 : 4;
+    static constexpr int NOPS = KIND == kTcBf16x3 ? 4 : 2;
     // Promotion: the tensor-core accumulator is restarted every CHUNK_KT
     // k-tiles (128 values of k) and added into FP32 registers with IEEE
     // round-to-nearest, so the accumulation error grows with 128, not K.
@@ -133,14 +140,18 @@ struct Tc {
     // C is written in whole 128-byte row segments.
     static constexpr int STG_LD = 36;
     static constexpr int STG_WARP_FLOATS = 32 * STG_LD;
-    static constexpr int STG_OFFSET = (BAR_OFFSET + BAR_BYTES + 15) / 16 * 16;
+    // 3xF16: each epilogue warp's copy of the current chunk's column scales
+    // (COLS floats), written and read by that warp only.
+    static constexpr int SCL_OFFSET = (BAR_OFFSET + BAR_BYTES + 15) / 16 * 16;
+    static constexpr int SCL_BYTES = SCALED ? EPI_WARPS * COLS * 4 : 0;
+    static constexpr int STG_OFFSET = SCL_OFFSET + SCL_BYTES;
     static constexpr int STG_END = STG_OFFSET + EPI_WARPS * STG_WARP_FLOATS * 4;
     static constexpr bool STAGE_C = STG_END + 1024 <= 232448;
-    static constexpr int SMEM_BYTES = (STAGE_C ? STG_END : BAR_OFFSET + BAR_BYTES) + 1024;
+    static constexpr int SMEM_BYTES = (STAGE_C ? STG_END : STG_OFFSET) + 1024;
     // Instruction descriptor: D = F32 (bits 4-5 = 1), A/B format (bits 7-9,
-    // 10-12: TF32 = 2, BF16 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
-    // bit 17, M >> 4 at bit 24.
-    static constexpr uint32_t FMT = KIND == kTcTf32 ? 2u : 1u;
+    // 10-12: TF32 = 2, BF16 = 1, F16 = 0), both K-major (bits 15, 16 = 0),
+    // N >> 3 at bit 17, M >> 4 at bit 24.
+    static constexpr uint32_t FMT = KIND == kTcTf32 ? 2u : (KIND == kTcBf16x3 ? 1u : 0u);
     static constexpr uint32_t IDESC =
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     static constexpr uint32_t IDESC_W =
@@ -161,11 +172,11 @@ struct Tc {
 // right half += A_pa B_pb+1); otherwise N = BN into the right half.  The
 // first MMA is wide, so the zeroing of a chunk's first k step covers both
 // halves.
-//   3xTF32: A0 [B0|B1] (hh, hl), A1 B0 (lh).
+//   3xTF32, 3xF16: A0 [B0|B1] (hh, hl), A1 B0 (lh).
 //   BF16x3: A0 [B0|B1], A1 [B0|B1], A0 B2, A2 B0  (the six b_i b_j, i+j <= 2).
 template <int KIND>
 __device__ __forceinline__ void tc_op(int q, int &pa, int &pb, bool &wide) {
-    if constexpr (KIND == kTcTf32) {
+    if constexpr (KIND != kTcBf16x3) {
         constexpr int a[2] = {0, 1}, b[2] = {0, 0};
         pa = a[q];
         pb = b[q];
@@ -206,6 +217,11 @@ struct TcArgs {
     // CTA b's partial tile (partials + b * BM * BN, row-major BM x BN).
     unsigned *sk_words;
     float *sk_partials;
+    // 3xF16: 2^-S of row r (column n), chunk c at scale_a[c * ld_sa + r]
+    // (scale_b[c * ld_sb + n]); ld_sa >= round_up(M, 128), ld_sb >= round_up(N, 128).
+    const float *scale_a;
+    const float *scale_b;
+    int64_t ld_sa, ld_sb;
     // Stream-K finisher's wait for a contributor's flag: time limit (ns) and
     // the offset of the awaited value from epoch + 1 (0; 1 only under the
     // test hook pt_debug_streamk_wait, which makes the value one nobody writes).
@@ -375,7 +391,10 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     const int kt_total = (args.K + BK - 1) / BK;
     int kt0 = 0, nkt = kt_total;
     if constexpr (V::SPLITK > 1) {
-        const int per = (kt_total + V::SPLITK - 1) / V::SPLITK;
+        int per = (kt_total + V::SPLITK - 1) / V::SPLITK;
+        // 3xF16: a CTA's k range starts on a 128-k chunk, so its chunks are
+        // the split kernel's scale chunks.
+        if constexpr (V::SCALED) per = (per + CKT - 1) / CKT * CKT;
         kt0 = (int)blockIdx.z * per;
         const int kt_end = kt0 + per < kt_total ? kt0 + per : kt_total;
         nkt = kt_end > kt0 ? kt_end - kt0 : 0;
@@ -565,11 +584,29 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         int g = 0;  // k-tiles converted (fused versions)
         unsigned epoch1 = 0;  // stream-K: this launch's flag value
         if constexpr (V::STREAMK != 0) epoch1 = ld_acquire_u32(args.sk_words) + 1u;
+        // 3xF16: this warp's copy of the chunk's column scales.
+        float *scl = reinterpret_cast<float *>(smem_raw + (sbase - raw) + V::SCL_OFFSET) + warp * COLS;
         for (int i = 0; epi_ok && i < nseg; ++i) {
             int t, c0, c1;
             work.seg(i, t, c0, c1);
 #pragma unroll
             for (int j = 0; j < COLS; ++j) racc[j] = 0.f;
+            // 3xF16: scales of chunk ch (row scale of this thread's row, four
+            // column scales per lane), loaded one chunk ahead.
+            int64_t srow = 0, scol = 0;
+            float sa_next = 1.f;
+            float4 sb_next = make_float4(1.f, 1.f, 1.f, 1.f);
+            if constexpr (V::SCALED) {
+                int sm0, sn0;
+                tc_tile_coords<V>(t, tiles_m, tiles_n, sm0, sn0);
+                srow = sm0 + sub * 32 + lane;
+                scol = sn0 + grp * COLS + 4 * lane;
+                const int64_t gc = kt0 / CKT + c0;
+                if (c0 < c1) {
+                    sa_next = args.scale_a[gc * args.ld_sa + srow];
+                    if (4 * lane < COLS) sb_next = *reinterpret_cast<const float4 *>(args.scale_b + gc * args.ld_sb + scol);
+                }
+            }
             constexpr int DEFER = V::EPI_CONV ? 1 : 0;  // drains run one chunk behind the conversions
             for (int ch = c0; ch < c1 + DEFER; ++ch) {
                 if constexpr (V::EPI_CONV) {
@@ -591,6 +628,20 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     if (ch == c0) continue;
                 }
                 const int b = c & 1;
+                float sa = 1.f;
+                if constexpr (V::SCALED) {
+                    // This chunk's scales into place; the next chunk's loads go out.
+                    sa = sa_next;
+                    __syncwarp();  // the previous chunk's reads of scl are done
+                    if (4 * lane < COLS) *reinterpret_cast<float4 *>(scl + 4 * lane) = sb_next;
+                    __syncwarp();
+                    if (ch + 1 < c1) {
+                        const int64_t gc = kt0 / CKT + ch + 1;
+                        sa_next = args.scale_a[gc * args.ld_sa + srow];
+                        if (4 * lane < COLS)
+                            sb_next = *reinterpret_cast<const float4 *>(args.scale_b + gc * args.ld_sb + scol);
+                    }
+                }
                 const bool ok = mbar_wait_bounded(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) {
                     epi_ok = false;
@@ -600,12 +651,29 @@ __global__ void __launch_bounds__(V::THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < COLS; j += 32) {
                     uint32_t r[32];
-                    tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + j), r);
+                    if constexpr (V::SCALED) {
+                        // Each half times 2^-S_A * 2^-S_B (a power of two: exact),
+                        // added into the FP32 registers with one rounding.
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
-                    tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + BN + j), r);
+                        for (int h = 0; h < 2; ++h) {
+                            tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + h * BN + j), r);
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
+                            for (int q = 0; q < 32; q += 4) {
+                                const float4 sb = *reinterpret_cast<const float4 *>(scl + j + q);
+                                racc[j + q] = fmaf(__uint_as_float(r[q]), sa * sb.x, racc[j + q]);
+                                racc[j + q + 1] = fmaf(__uint_as_float(r[q + 1]), sa * sb.y, racc[j + q + 1]);
+                                racc[j + q + 2] = fmaf(__uint_as_float(r[q + 2]), sa * sb.z, racc[j + q + 2]);
+                                racc[j + q + 3] = fmaf(__uint_as_float(r[q + 3]), sa * sb.w, racc[j + q + 3]);
+                            }
+                        }
+                    } else {
+                        tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + j), r);
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
+                        tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + BN + j), r);
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();

@@ -2,11 +2,12 @@
 
 Shapes M = N = K in {1024, 4096, 8192}, 8192 x 8192 x 256 and
 256 x 8192 x 8192; entries s * 2^U[-10,10] with a random sign s (A from seed
-3, B from seed 4).  Every tensor-core version (3xTF32 and BF16x3, all
-schedules) and a sample of the FP32 SIMT family run each shape; sampled full
-rows (all rows when M <= 1024) are compared with the FP64 oracle.  Bound:
-normalised error <= 2e-6 for every kind (FP32 SIMT and 3xTF32 by the
-accuracy target; BF16x3 with six products is held to the same bound).
+3, B from seed 4).  Every tensor-core version (3xTF32, BF16x3 and scaled
+3xF16, all schedules) and a sample of the FP32 SIMT family run each shape;
+sampled full rows (all rows when M <= 1024) are compared with the FP64
+oracle.  Bound: normalised error <= 2e-6 for every kind (FP32 SIMT and
+3xTF32 by the accuracy target; BF16x3 and 3xF16, of the same or higher
+precision, are held to the same bound).
 
 With PT_PARITY_REPORT set to a file path, the per-shape, per-kind maximum
 errors and the worst variant of each kind are written there as JSON.
@@ -28,7 +29,7 @@ torch = pytest.importorskip("torch")
 pt = pytest.importorskip("paper_2507_15277_gb300")
 
 DEV = "cuda:0"
-KINDS = {0: "fp32_simt", 1: "3xtf32", 2: "bf16x3"}
+KINDS = {0: "fp32_simt", 1: "3xtf32", 2: "bf16x3", 3: "3xf16"}
 _report = {}
 
 

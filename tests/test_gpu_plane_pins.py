@@ -12,12 +12,14 @@ result) and whose entries need two or three planes:
 * wide integers (workloads.wide_int_operands): 18-bit, 9-bit and +-1
   entries arranged so that every product the BF16x3 split keeps (b_i b_j,
   i + j <= 2) and every one the 3xTF32 split keeps (hi hi, hi lo, lo hi) is
-  non-zero for many outputs, and every product they drop is zero (the CPU
-  tests in test_split_planes.py establish both facts).
+  non-zero for many outputs, and every product they drop is zero; the same
+  holds for the scaled 3xF16 split (h0 h0, h0 h1, h1 h0), whose per-chunk
+  power-of-two scales change no significand bit (the CPU tests in
+  test_split_planes.py establish these facts).
 
 Every registered variant -- FP32 SIMT (with and without cluster split-K),
-3xTF32 and BF16x3 in every schedule (persistent, stream-K, cluster split-K
-2/4/8), with fused A or B splitting and 32-column tiles -- must reproduce the
+3xTF32, BF16x3 and 3xF16 in every schedule (persistent, stream-K, cluster
+split-K 2/4/8), with fused A or B splitting and 32-column tiles -- must reproduce the
 FP64 oracle's result bit for bit.  The operation is the paper's GEMM
 (Section V-B); the split is an extension of the variant family.
 """

@@ -48,7 +48,8 @@ def test_registry_rules():
         assert d["smem_bytes"] <= 232448
         if d["kind"] != 0:
             # split-precision tensor-core variants: 128-row tiles, TMA, any layout
-            assert d["kind"] in (1, 2) and d["bm"] == 128 and d["bn"] in (32, 64, 128)
+            assert d["kind"] in (1, 2, 3) and d["bm"] == 128 and d["bn"] in (32, 64, 128)
+            assert d["name"].startswith({1: "tc3xtf32_", 2: "tcbf16x3_", 3: "tc3xf16_"}[d["kind"]])
             # fused versions read B (or A) themselves: transB (transA) = 'N' only; the others take any layout
             assert d["loader"] == 1 and d["trans_mask"] == (5 if "_fb" in d["name"] else 3 if "_fa" in d["name"] else 15)
             # epilogue + producer + MMA warps (+ four converter warps when B is split in the kernel)
@@ -71,7 +72,7 @@ def test_registry_rules():
         assert d["smem_bytes"] <= 232448
         assert d["bm"] % d["splitk"] == 0
         assert d["tm"] * d["tn"] <= 64
-    assert {pt.variant(i)["kind"] for i in range(n)} == {0, 1, 2}
+    assert {pt.variant(i)["kind"] for i in range(n)} == {0, 1, 2, 3}
     assert all(pt.variant(i)["kind"] == 0 for i in range(len(simt)))  # SIMT family first
     d0 = pt.variant(pt.default_variant())
     assert (d0["bm"], d0["bn"], d0["bk"], d0["vec"], d0["loader"], d0["trans_mask"]) == (128, 128, 8, 1, 0, 15)
