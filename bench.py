@@ -55,12 +55,14 @@ def parse():
     p.add_argument("--single", default=None, metavar="M,N,K",
                    help="profiling mode: run one variant (--variant) on one shape, no tuning")
     p.add_argument("--variant", default=None, help="variant name for --single")
-    p.add_argument("--report", default=None, choices=["splitprec", "grouped", "stability", "oracle", "autograd"],
+    p.add_argument("--report", default=None,
+                   choices=["splitprec", "grouped", "stability", "oracle", "autograd", "noalloc"],
                    help="splitprec: tensor-core split-precision vs FP32 SIMT on the split-precision shapes; "
                         "grouped: 512 uneven problems, persistent grouped launch vs separate launches; "
                         "stability: the sweep tuned twice, rank agreement of the two timing tables; "
                         "oracle: the FP64 CPU oracle timed at 256^3, 1024^3 and 4096^3; "
-                        "autograd: Y = X W forward and backward through the tuned SGEMM")
+                        "autograd: Y = X W forward and backward through the tuned SGEMM; "
+                        "noalloc: the allocation-free entry point against its registry twin")
     return p.parse_args()
 
 
@@ -194,6 +196,56 @@ def report_splitprec(args):
     torch.backends.cuda.matmul.allow_tf32 = False
     print(json.dumps({"mode": "splitprec", "inputs": "sign * 2^U[-10,10], seed 3", "tune_s": tune_s,
                       "tf32_cublas_tflops_8192": tf32, "shapes": res}))
+    return 0
+
+
+def report_noalloc(args):
+    """pt_sgemm_3xtf32_noalloc against the registry's tc3xtf32_m128n128_p3
+    (the same split and kernel with a library workspace) on 1536^3 and
+    1024 x 2048 x 1024, U[-1,1]: mean call time over 50 launches each,
+    CUDA events on one stream."""
+    import ctypes
+
+    import torch
+
+    import paper_2507_15277_gb300 as pt
+    from paper_2507_15277_gb300 import _lib
+    from workloads import matrix
+    dev = torch.device("cuda", 0)
+    lib = _lib.lib()
+    stream = torch.cuda.Stream(dev)
+    vid = pt.variant_by_name("tc3xtf32_m128n128_p3")
+    res = []
+    for (M, N, K) in ((1536, 1536, 1536), (1024, 2048, 1024)):
+        A = torch.from_numpy(matrix("uniform", 1, M, K)).to(dev)
+        B = torch.from_numpy(matrix("uniform", 2, K, N)).to(dev)
+        C = torch.empty((M, N), device=dev)
+
+        def noalloc():
+            rc = lib.pt_sgemm_3xtf32_noalloc(b"N", b"N", M, N, K, 1.0, ctypes.c_void_p(A.data_ptr()), K,
+                                             ctypes.c_void_p(B.data_ptr()), N, 0.0, ctypes.c_void_p(C.data_ptr()),
+                                             N, ctypes.c_void_p(stream.cuda_stream))
+            if rc:
+                raise RuntimeError(lib.pt_last_error())
+
+        def twin():
+            pt.sgemm(A, B, C, variant=vid, stream=stream)
+
+        entry = {"shape": [M, N, K]}
+        for name, fn in (("noalloc", noalloc), ("tc3xtf32_m128n128_p3", twin)):
+            with torch.cuda.stream(stream):
+                for _ in range(5):
+                    fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(50):
+                    fn()
+                e1.record(stream)
+                stream.synchronize()
+            ms = e0.elapsed_time(e1) / 50
+            entry[name] = {"ms": ms, "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12}
+        res.append(entry)
+    print(json.dumps({"mode": "noalloc", "shapes": res}))
     return 0
 
 
@@ -769,6 +821,8 @@ def main():
         return report_oracle(args)
     if args.report == "autograd":
         return report_autograd(args)
+    if args.report == "noalloc":
+        return report_noalloc(args)
 
     import numpy as np
     import torch
@@ -993,6 +1047,50 @@ def main():
     e2e_wall = time.perf_counter() - t0
     e2e_ms = e0.elapsed_time(e1)
 
+    # Overlap of the three stages in one more (untimed) pipelined step: timing
+    # events around every copy and GEMM group give each stage's busy time;
+    # with full overlap the step takes about the longest stage, without any
+    # it takes their sum.
+    ev_t = {}
+
+    def timed_e2e_step():
+        for g, (a, b) in enumerate(groups):
+            ts = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            ev_t[g] = ts
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(ev_done[g])
+                ts[0].record(s_in)
+                dev_in[in_off[a]:in_off[b]].copy_(host_in[in_off[a]:in_off[b]], non_blocking=True)
+                ts[1].record(s_in)
+                ev_in[g].record(s_in)
+            stream.wait_event(ev_in[g])
+            stream.wait_event(ev_out[g])
+            ts[2].record(stream)
+            for i in range(a, b):
+                pt.sgemm(devA[i], devB[i], devC[i], stream=stream)
+            ts[3].record(stream)
+            ev_done[g].record(stream)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_done[g])
+                ts[4].record(s_out)
+                host_out[out_off[a]:out_off[b]].copy_(dev_out[out_off[a]:out_off[b]], non_blocking=True)
+                ts[5].record(s_out)
+                ev_out[g].record(s_out)
+
+    torch.cuda.synchronize()
+    t_first = torch.cuda.Event(enable_timing=True)
+    t_first.record(stream)
+    s_in.wait_stream(stream)
+    timed_e2e_step()
+    stream.wait_stream(s_out)
+    t_last = torch.cuda.Event(enable_timing=True)
+    t_last.record(stream)
+    torch.cuda.synchronize()
+    busy = [sum(ev_t[g][2 * st].elapsed_time(ev_t[g][2 * st + 1]) for g in ev_t) for st in range(3)]
+    overlap = {"step_ms": t_first.elapsed_time(t_last), "h2d_busy_ms": busy[0], "gemm_busy_ms": busy[1],
+               "d2h_busy_ms": busy[2]}
+    overlap["overlap_factor"] = sum(busy) / overlap["step_ms"]
+
     # Copy-engine rates alone (context for e2e): one step's input and output
     # copies, each direction by itself.
     def copies_ms(fn, reps=3):
@@ -1123,10 +1221,12 @@ def main():
                               "splits with FP32 accumulation",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "clocks": clk,
-        "gpu_launches": args.steps * sum(1 if pt.variant(p)["kind"] == 0 else 2 for p in picks),
+        # per call: SIMT one kernel; split + GEMM; 3xF16 row maxima + split + GEMM
+        "gpu_launches": args.steps * sum({0: 1, 3: 3}.get(pt.variant(p)["kind"], 2) for p in picks),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "wall_s": e2e_wall, "ms_per_step": e2e_ms / args.steps,
                 "h2d_gbs_alone": h2d / (h2d_ms * 1e-3) / 1e9, "d2h_gbs_alone": d2h / (d2h_ms * 1e-3) / 1e9,
+                "overlap": overlap,
                 "pipeline": "3 streams over %d groups of consecutive shapes (about equal bytes), one copy per group "
                             "and direction: H2D of group g+1 | GEMMs of group g | D2H of group g-1" % len(groups)},
         "roofline": roofline,

@@ -10,10 +10,11 @@ planes and drop the smallest cross products:
           b2 = RN_bf16(x - b0 - b1);
           a*b ~ sum of a_i*b_j over i + j <= 2       (a1b2, a2b1, a2b2 dropped)
 
-  3xF16 (scaled): each row of op(A) and each column of op(B) is cut into
-          chunks of 128 values of k; a chunk is multiplied by 2^S with
-          S = 14 - floor(log2 m), m its largest magnitude, clamped to
-          [-63, 63] (63 when m = 0); then x' = h0 + h1 with h0 = RN_f16(x'),
+  3xF16 (scaled): k is cut into chunks of 128 values; chunk c of row i of
+          op(A) is multiplied by 2^S with S = 14 - floor(log2 m), m its
+          largest magnitude, clamped to [-63, 63] (63 when m = 0); chunk c of
+          a group of 32 consecutive columns of op(B) likewise, m over the
+          group's chunk.  Then x' = h0 + h1 with h0 = RN_f16(x'),
           h1 = RN_f16(x' - h0) and the products kept as in 3xTF32; each
           chunk's sum is multiplied back by 2^-S_A 2^-S_B.
 
@@ -60,32 +61,34 @@ def bf16x3_planes(x):
     return b0, b1, b2
 
 
-def f16_chunk_scales(X, chunk: int = 128) -> np.ndarray:
-    """Exponents S[r, c] of the 3xF16 split of the rows of X (rows x K):
-    2^S brings the largest magnitude of chunk c of row r into [2^14, 2^15)."""
+def f16_chunk_scales(X, group: int = 1, chunk: int = 128) -> np.ndarray:
+    """Exponents S[g, c] of the 3xF16 split of X (rows x K), for groups of
+    `group` consecutive rows (1 for op(A); 32 for the rows of op(B)^T) and
+    chunks of `chunk` values of k: 2^S brings the largest magnitude of the
+    group's chunk into [2^14, 2^15)."""
     X = np.abs(np.asarray(X, dtype=np.float64))
     rows, K = X.shape
-    nch = -(-K // chunk)
-    S = np.empty((rows, nch), dtype=np.int64)
-    for c in range(nch):
-        m = X[:, c * chunk:(c + 1) * chunk].max(axis=1) if K else np.zeros(rows)
-        with np.errstate(divide="ignore"):
-            e = np.where(m > 0, np.floor(np.log2(np.where(m > 0, m, 1.0))), -1000)
-        S[:, c] = np.clip(14 - e, -63, 63).astype(np.int64)
+    ng, nch = -(-rows // group), -(-K // chunk)
+    S = np.empty((ng, nch), dtype=np.int64)
+    for g in range(ng):
+        for c in range(nch):
+            m = X[g * group:(g + 1) * group, c * chunk:(c + 1) * chunk].max(initial=0.0)
+            S[g, c] = 63 if m == 0 else int(np.clip(14 - np.floor(np.log2(m)), -63, 63))
     return S
 
 
-def f16x2_planes_scaled(X, chunk: int = 128):
-    """(h0, h1, S) of the scaled 3xF16 split of the rows of X: h0 + h1 is
-    X[r, k] * 2^S[r, k // chunk] on the FP16 grid (FP64 arrays)."""
+def f16x2_planes_scaled(X, group: int = 1, chunk: int = 128):
+    """(h0, h1, E) of the scaled 3xF16 split of the rows of X: h0 + h1 is
+    X[r, k] * 2^E[r, k] on the FP16 grid (FP64 arrays), E[r, k] the scale
+    exponent of r's group and k's chunk."""
     X = np.asarray(X, dtype=np.float64)
-    S = f16_chunk_scales(X, chunk)
-    scale = np.ldexp(1.0, np.repeat(S, chunk, axis=1)[:, :X.shape[1]])
-    xs = X * scale
+    S = f16_chunk_scales(X, group, chunk)
+    E = np.repeat(np.repeat(S, group, axis=0), chunk, axis=1)[:X.shape[0], :X.shape[1]]
+    xs = X * np.ldexp(1.0, E)
     with np.errstate(over="ignore", invalid="ignore"):   # beyond FP16's range: inf, as the kernel
         h0 = xs.astype(np.float16).astype(np.float64)
         h1 = (xs - h0).astype(np.float16).astype(np.float64)
-    return h0, h1, S
+    return h0, h1, E
 
 
 BF16X3_KEPT = [(0, 0), (0, 1), (1, 0), (1, 1), (0, 2), (2, 0)]

@@ -1,6 +1,6 @@
 // Split kernel of the tensor-core versions: FP32 operands to K-major
 // low-precision planes (3xTF32: hi, lo; BF16x3: b0, b1, b2; scaled 3xF16:
-// h0, h1 of the value times a power-of-two scale per row and 128 values of k)
+// h0, h1 of the value times a power-of-two scale per 128 values of k)
 // in a workspace that the GEMM kernel reads through TMA.
 #pragma once
 
@@ -15,15 +15,17 @@ constexpr int kTcTf32 = 0;
 constexpr int kTcBf16x3 = 1;
 constexpr int kTcF16s = 2;  // scaled FP16 split, three products (3xTF32's precision, FP16 rate)
 
-// Scaled FP16 split: every row of an operand is cut into chunks of 128
-// values of k; chunk c of row r is multiplied by s = 2^S(r, c) before the
-// split, with S = 14 - floor(log2 m), m = max |x| over the chunk, clamped to
-// [-63, 63] (S = 63 when m = 0), so the chunk's largest magnitude lands in
-// [2^14, 2^15) (FP16 holds up to 65504).  The GEMM multiplies the chunk's
-// product by 2^-S_A(row, c) * 2^-S_B(col, c), a power of two in
-// [2^-126, 2^126], exactly representable.  Chunk maxima in [2^-49, 2^78]
-// get the full scale; beyond 2^78 the planes overflow to infinity, below
-// 2^-49 the values keep fewer bits (as FP32 products of such values do).
+// Scaled FP16 split: k is cut into chunks of 128 values.  Chunk c of row r of
+// op(A) is multiplied by 2^S_A(r, c); chunk c of a group of 32 consecutive
+// columns g of op(B) (32 consecutive rows of the K-major B planes) by
+// 2^S_B(g, c).  S = 14 - floor(log2 m), m the largest magnitude in that
+// chunk of the row (of the 32 columns), clamped to [-63, 63] (63 when
+// m = 0), so that largest magnitude lands in [2^14, 2^15) (FP16 holds up to
+// 65504).  The GEMM multiplies each chunk's product by 2^-S_A * 2^-S_B, a
+// power of two in [2^-126, 2^126] (exact), when it drains the chunk.  Maxima
+// in [2^-49, 2^78] get the full scale; beyond 2^78 the planes overflow to
+// infinity, below 2^-49 the values keep fewer bits (as FP32 products of such
+// values do).
 constexpr int kF16ScaleMin = -63, kF16ScaleMax = 63;
 __device__ __forceinline__ int f16_scale_exp(float m) {
     const int e = (int)((__float_as_uint(m) >> 23) & 0xffu);  // biased exponent of m (0: zero or subnormal)
@@ -145,7 +147,8 @@ struct SplitOperand {
     unsigned char *ws;
     int64_t plane_bytes;
     int vec4;  // src and ld allow 16-byte loads
-    // Scaled FP16 split only: 2^-S of row r, chunk c at scale[c * ld_scale + r].
+    // Scaled FP16 split only: 2^-S of chunk c at scale[c * ld_scale + i], i the
+    // row (first operand) or the 32-row group (second operand).
     float *scale = nullptr;
     int64_t ld_scale = 0;
 };
@@ -159,23 +162,17 @@ struct SplitOperand {
 constexpr int SPLIT_KT = 4;
 constexpr int SPLIT_K_PER_BLOCK = 64 * SPLIT_KT;
 
-template <int KIND>
-__global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, const SplitOperand b, int K,
-                                                       int64_t pitch, int ya) {
-    __shared__ float tile[SPLIT_KT][64][33];
-    const bool first = (int)blockIdx.y < ya;
-    const SplitOperand &o = first ? a : b;
-    const int by = first ? (int)blockIdx.y : (int)blockIdx.y - ya;
+// The block's 32 rows x SPLIT_K_PER_BLOCK values of k starting at
+// (r0, kb) into x (thread t: row r0 + t / 8, values kb + 64 s + 8 (t % 8) + i of
+// slab s); values outside the operand are zero.  Transposed sources go
+// through shared memory so that both the loads and the later 16-byte plane
+// stores are contiguous.
+__device__ __forceinline__ void split_load_block(const SplitOperand &o, int K, int r0, int kb, int tid,
+                                                 float (&x)[SPLIT_KT][8], float (*tile)[64][33]) {
     const float *__restrict__ src = o.src;
     const int64_t ld = o.ld;
     const int rows = o.rows;
-    const int r0 = by * 32, kb = blockIdx.x * SPLIT_K_PER_BLOCK;
-    const int tid = threadIdx.x;
     const int r = r0 + (tid >> 3), kt8 = (tid & 7) * 8;
-    float x[SPLIT_KT][8];
-    // Launched with programmatic stream serialization: the previous kernel
-    // (e.g. a GEMM still reading the planes) completes first.
-    pdl_wait();
     if (o.trans) {
         // tile[t][kk][rr] <- X(r0 + rr, kb + 64 t + kk) = src[(kb + 64 t + kk) * ld + r0 + rr]
         float v[SPLIT_KT][2][4];
@@ -221,9 +218,28 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, con
             }
         }
     }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, const SplitOperand b, int K,
+                                                       int64_t pitch, int ya) {
+    __shared__ float tile[SPLIT_KT][64][33];
+    __shared__ float gmax[SPLIT_KT / 2][8];
+    const bool first = (int)blockIdx.y < ya;
+    const SplitOperand &o = first ? a : b;
+    const int by = first ? (int)blockIdx.y : (int)blockIdx.y - ya;
+    const int r0 = by * 32, kb = blockIdx.x * SPLIT_K_PER_BLOCK;
+    const int tid = threadIdx.x;
+    const int r = r0 + (tid >> 3), kt8 = (tid & 7) * 8;
+    float x[SPLIT_KT][8];
+    // Launched with programmatic stream serialization: the previous kernel
+    // (e.g. a GEMM still reading the planes) completes first.
+    pdl_wait();
+    split_load_block(o, K, r0, kb, tid, x, tile);
     if constexpr (KIND == kTcF16s) {
-        // Chunk scales: slabs 2c and 2c + 1 form chunk kb / 128 + c; the eight
-        // threads of a row (consecutive lanes) combine their maxima.
+        // Slabs 2c and 2c + 1 form chunk kb / 128 + c.  First operand: the
+        // maximum of each row's chunk (its eight threads are consecutive
+        // lanes); second operand: of the block's 32 rows (all threads).
         static_assert(SPLIT_KT % 2 == 0, "a block covers whole 128-k chunks");
 #pragma unroll
         for (int c = 0; c < SPLIT_KT / 2; ++c) {
@@ -232,23 +248,46 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, con
             for (int t = 2 * c; t < 2 * c + 2; ++t)
 #pragma unroll
                 for (int i = 0; i < 8; ++i) m = fmaxf(m, fabsf(x[t][i]));
-            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
-            const int S = f16_scale_exp(m);
-            const float s = pow2f(S);
 #pragma unroll
-            for (int t = 2 * c; t < 2 * c + 2; ++t)
+            for (int off = 1; off < 8; off <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+            if (!first) {
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+                if ((tid & 31) == 0) gmax[c][tid >> 5] = m;
+            }
+            if (first) {
+                const int S = f16_scale_exp(m);
+                const float sc = pow2f(S);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) x[t][i] *= s;
-            const int gc = kb / 128 + c;
-            if ((tid & 7) == 0 && r < rows && 128 * gc < pitch) o.scale[(int64_t)gc * o.ld_scale + r] = pow2f(-S);
+                for (int t = 2 * c; t < 2 * c + 2; ++t)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x[t][i] *= sc;
+                const int gc = kb / 128 + c;
+                if ((tid & 7) == 0 && r < o.rows && 128 * gc < pitch) o.scale[(int64_t)gc * o.ld_scale + r] = pow2f(-S);
+            }
+        }
+        if (!first) {
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < SPLIT_KT / 2; ++c) {
+                float m = gmax[c][0];
+#pragma unroll
+                for (int w = 1; w < 8; ++w) m = fmaxf(m, gmax[c][w]);
+                const int S = f16_scale_exp(m);
+                const float sc = pow2f(S);
+#pragma unroll
+                for (int t = 2 * c; t < 2 * c + 2; ++t)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x[t][i] *= sc;
+                const int gc = kb / 128 + c;
+                if (tid == 0 && 128 * gc < pitch) o.scale[(int64_t)gc * o.ld_scale + by] = pow2f(-S);
+            }
         }
     }
 #pragma unroll
     for (int t = 0; t < SPLIT_KT; ++t) {
         const int k = kb + 64 * t + kt8;
-        if (r < rows && k < pitch) split_store8<KIND>(o.ws, o.plane_bytes, pitch, r, k, x[t]);
+        if (r < o.rows && k < pitch) split_store8<KIND>(o.ws, o.plane_bytes, pitch, r, k, x[t]);
     }
     pdl_trigger();
 }

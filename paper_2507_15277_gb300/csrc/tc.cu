@@ -114,11 +114,12 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
         }
     }
     // Workspace: stream-K header, stream-K partial tiles, the planes, then
-    // (3xF16) the chunk scales of A and B, [chunk][row] with padded rows.
+    // (3xF16) the chunk scales of op(A) rows, [chunk][round_up(M, 128)], and
+    // of op(B) 32-column groups, [chunk][round_up(N, 128) / 32].
     const int64_t header = align256((int64_t)kSkHeaderBytes);
     const int64_t partials = V::STREAMK ? align256(grid * V::BM * V::BN * 4) : 0;
     const int64_t nchk = ((int64_t)a.K + 127) / 128;
-    const int64_t ld_sa = ((int64_t)a.M + 127) / 128 * 128, ld_sb = ((int64_t)a.N + 127) / 128 * 128;
+    const int64_t ld_sa = ((int64_t)a.M + 127) / 128 * 128, ld_sb = ((int64_t)a.N + 127) / 128 * 4;
     const int64_t sa_bytes = V::SCALED ? align256(nchk * ld_sa * 4) : 0;
     const int64_t sb_bytes = V::SCALED ? align256(nchk * ld_sb * 4) : 0;
     const size_t need =

@@ -8,13 +8,15 @@
 //   BF16x3:  x = b0 + b1 + b2, b0 = RN_bf16(x), b1 = RN_bf16(x - b0),
 //            b2 = RN_bf16(x - b0 - b1);
 //            a*b ~ sum of the six b_i*b_j with i + j <= 2 (kind::f16 with BF16, 6 MMAs)
-//   3xF16:   x' = x * 2^S (S per row and 128 values of k, so that the chunk's
-//            largest |x'| is in [2^14, 2^15)), x' = h0 + h1 on the FP16 grid
-//            (11-bit significands, as TF32); a'*b' ~ h0 h0 + h0 h1 + h1 h0
-//            (kind::f16 with F16, 3 MMAs at the BF16 rate); each chunk's
-//            product is multiplied by 2^-S_A * 2^-S_B when it is drained.
+//   3xF16:   x' = x * 2^S (S per 128 values of k and row of op(A), or group
+//            of 32 columns of op(B), so that the largest |x'| there is in
+//            [2^14, 2^15)), x' = h0 + h1 on the FP16 grid (11-bit
+//            significands, as TF32); a'*b' ~ h0 h0 + h0 h1 + h1 h0 (kind::f16
+//            with F16, 3 MMAs at the BF16 rate); each 128-k partial product is
+//            multiplied by 2^-S_A * 2^-S_B when it is drained.
 // The dropped terms are O(2^-22) (3xTF32, 3xF16) and O(2^-24) (BF16x3)
-// relative to |a*b| (3xF16: relative to the chunk's largest |a| |b|), so the
+// relative to |a*b| (3xF16: relative to the largest |a| of the row's chunk
+// times the largest |b| of the 32 columns' chunk), so the
 // result is FP32-accurate; these variants join the FP32 SIMT family as
 // further versions of the same operation.
 //
@@ -87,7 +89,7 @@ struct Tc {
     // FP32 partial tiles are summed through distributed shared memory in
     // cluster-rank order (the pipeline's shared memory is reused for them).
     static constexpr int RED_LD = BN + 4;
-    static constexpr bool SCALED = KIND == kTcF16s;       // per-chunk scales applied when draining
+    static constexpr bool SCALED = KIND == kTcF16s;       // chunk scales applied when draining
     static constexpr int ELEM = KIND == kTcTf32 ? 4 : 2;  // bytes per plane element
     static constexpr int P = KIND == kTcBf16x3 ? 3 : 2;   // planes per operand
     static constexpr int BK = SWZ / ELEM;                 // one swizzle row per tile row
@@ -140,11 +142,7 @@ struct Tc {
     // C is written in whole 128-byte row segments.
     static constexpr int STG_LD = 36;
     static constexpr int STG_WARP_FLOATS = 32 * STG_LD;
-    // 3xF16: each epilogue warp's copy of the current chunk's column scales
-    // (COLS floats), written and read by that warp only.
-    static constexpr int SCL_OFFSET = (BAR_OFFSET + BAR_BYTES + 15) / 16 * 16;
-    static constexpr int SCL_BYTES = SCALED ? EPI_WARPS * COLS * 4 : 0;
-    static constexpr int STG_OFFSET = SCL_OFFSET + SCL_BYTES;
+    static constexpr int STG_OFFSET = (BAR_OFFSET + BAR_BYTES + 15) / 16 * 16;
     static constexpr int STG_END = STG_OFFSET + EPI_WARPS * STG_WARP_FLOATS * 4;
     static constexpr bool STAGE_C = STG_END + 1024 <= 232448;
     static constexpr int SMEM_BYTES = (STAGE_C ? STG_END : STG_OFFSET) + 1024;
@@ -164,6 +162,7 @@ struct Tc {
     // wave's A and B panels stay in L2.
     static constexpr int GROUP_M = 8;
     static_assert(TMEM_COLS <= 512, "tensor memory columns");
+    static_assert(EPI_WARPS <= 8, "stream-K flag slots per CTA");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
@@ -212,13 +211,14 @@ struct TcArgs {
     int vec4;  // C and ldc allow 16-byte stores
     int *err;
     // Stream-K: words[0] = launches completed on this workspace (the epoch),
-    // words[1] = CTAs of this launch that have finished, words[kSkFlags + 4b
+    // words[1] = CTAs of this launch that have finished, words[kSkFlags + 8b
     // + w] = epoch + 1 once epilogue warp w of CTA b has written its rows of
     // CTA b's partial tile (partials + b * BM * BN, row-major BM x BN).
     unsigned *sk_words;
     float *sk_partials;
-    // 3xF16: 2^-S of row r (column n), chunk c at scale_a[c * ld_sa + r]
-    // (scale_b[c * ld_sb + n]); ld_sa >= round_up(M, 128), ld_sb >= round_up(N, 128).
+    // 3xF16: 2^-S of chunk c (128 values of k) of row r of op(A) at
+    // scale_a[c * ld_sa + r] (ld_sa >= round_up(M, 128)), and of the 32-column
+    // group g of op(B) at scale_b[c * ld_sb + g] (ld_sb >= round_up(N, 128) / 32).
     const float *scale_a;
     const float *scale_b;
     int64_t ld_sa, ld_sb;
@@ -231,7 +231,8 @@ struct TcArgs {
 
 constexpr int kSkFlags = 32;                  // first flag word
 constexpr int kSkMaxGrid = 2048;              // flag slots (CTAs)
-constexpr size_t kSkHeaderBytes = 4 * (kSkFlags + 4 * kSkMaxGrid);
+constexpr int kSkFlagsPerCta = 8;             // one per epilogue warp (at most 8)
+constexpr size_t kSkHeaderBytes = 4 * (kSkFlags + kSkFlagsPerCta * kSkMaxGrid);
 
 // Work of one CTA as segments (tile t, chunks [c0, c1) of the tile's k range;
 // a chunk is 128 values of k).  Tile mode: tiles t_first, t_first + t_step,
@@ -584,27 +585,28 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         int g = 0;  // k-tiles converted (fused versions)
         unsigned epoch1 = 0;  // stream-K: this launch's flag value
         if constexpr (V::STREAMK != 0) epoch1 = ld_acquire_u32(args.sk_words) + 1u;
-        // 3xF16: this warp's copy of the chunk's column scales.
-        float *scl = reinterpret_cast<float *>(smem_raw + (sbase - raw) + V::SCL_OFFSET) + warp * COLS;
         for (int i = 0; epi_ok && i < nseg; ++i) {
             int t, c0, c1;
             work.seg(i, t, c0, c1);
 #pragma unroll
             for (int j = 0; j < COLS; ++j) racc[j] = 0.f;
-            // 3xF16: scales of chunk ch (row scale of this thread's row, four
-            // column scales per lane), loaded one chunk ahead.
-            int64_t srow = 0, scol = 0;
-            float sa_next = 1.f;
-            float4 sb_next = make_float4(1.f, 1.f, 1.f, 1.f);
+            // 3xF16: this thread's row scale and its COLS / 32 column-group
+            // scales for chunk ch, loaded one chunk ahead.
+            constexpr int NG = V::SCALED ? COLS / 32 : 1;
+            int64_t srow = 0, sgrp = 0;
+            float sa_next = 1.f, sb_next[NG];
+#pragma unroll
+            for (int q = 0; q < NG; ++q) sb_next[q] = 1.f;
             if constexpr (V::SCALED) {
                 int sm0, sn0;
                 tc_tile_coords<V>(t, tiles_m, tiles_n, sm0, sn0);
                 srow = sm0 + sub * 32 + lane;
-                scol = sn0 + grp * COLS + 4 * lane;
-                const int64_t gc = kt0 / CKT + c0;
+                sgrp = (sn0 + grp * COLS) / 32;
                 if (c0 < c1) {
+                    const int64_t gc = kt0 / CKT + c0;
                     sa_next = args.scale_a[gc * args.ld_sa + srow];
-                    if (4 * lane < COLS) sb_next = *reinterpret_cast<const float4 *>(args.scale_b + gc * args.ld_sb + scol);
+#pragma unroll
+                    for (int q = 0; q < NG; ++q) sb_next[q] = args.scale_b[gc * args.ld_sb + sgrp + q];
                 }
             }
             constexpr int DEFER = V::EPI_CONV ? 1 : 0;  // drains run one chunk behind the conversions
@@ -628,18 +630,18 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     if (ch == c0) continue;
                 }
                 const int b = c & 1;
-                float sa = 1.f;
+                float sc[NG];
+#pragma unroll
+                for (int q = 0; q < NG; ++q) sc[q] = 1.f;
                 if constexpr (V::SCALED) {
-                    // This chunk's scales into place; the next chunk's loads go out.
-                    sa = sa_next;
-                    __syncwarp();  // the previous chunk's reads of scl are done
-                    if (4 * lane < COLS) *reinterpret_cast<float4 *>(scl + 4 * lane) = sb_next;
-                    __syncwarp();
+                    // This chunk's scale per 32-column group; the next chunk's loads go out.
+#pragma unroll
+                    for (int q = 0; q < NG; ++q) sc[q] = sa_next * sb_next[q];
                     if (ch + 1 < c1) {
                         const int64_t gc = kt0 / CKT + ch + 1;
                         sa_next = args.scale_a[gc * args.ld_sa + srow];
-                        if (4 * lane < COLS)
-                            sb_next = *reinterpret_cast<const float4 *>(args.scale_b + gc * args.ld_sb + scol);
+#pragma unroll
+                        for (int q = 0; q < NG; ++q) sb_next[q] = args.scale_b[gc * args.ld_sb + sgrp + q];
                     }
                 }
                 const bool ok = mbar_wait_bounded(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), kWaitLimitNs);
@@ -652,20 +654,15 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 for (int j = 0; j < COLS; j += 32) {
                     uint32_t r[32];
                     if constexpr (V::SCALED) {
-                        // Each half times 2^-S_A * 2^-S_B (a power of two: exact),
+                        // (left + right) * 2^-S_A * 2^-S_B (a power of two: exact),
                         // added into the FP32 registers with one rounding.
+                        const float s32 = sc[j / 32];
+                        uint32_t r2[32];
+                        tmem_ld32x2(lane_base + (uint32_t)(b * V::ACC_COLS + j),
+                                    lane_base + (uint32_t)(b * V::ACC_COLS + BN + j), r, r2);
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + h * BN + j), r);
-#pragma unroll
-                            for (int q = 0; q < 32; q += 4) {
-                                const float4 sb = *reinterpret_cast<const float4 *>(scl + j + q);
-                                racc[j + q] = fmaf(__uint_as_float(r[q]), sa * sb.x, racc[j + q]);
-                                racc[j + q + 1] = fmaf(__uint_as_float(r[q + 1]), sa * sb.y, racc[j + q + 1]);
-                                racc[j + q + 2] = fmaf(__uint_as_float(r[q + 2]), sa * sb.z, racc[j + q + 2]);
-                                racc[j + q + 3] = fmaf(__uint_as_float(r[q + 3]), sa * sb.w, racc[j + q + 3]);
-                            }
-                        }
+                        for (int q = 0; q < 32; ++q)
+                            racc[j + q] = fmaf(__uint_as_float(r[q]) + __uint_as_float(r2[q]), s32, racc[j + q]);
                     } else {
                         tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + j), r);
 #pragma unroll
@@ -691,7 +688,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     pw[(q / 4) * 32] = make_float4(racc[q], racc[q + 1], racc[q + 2], racc[q + 3]);
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) st_release_u32(args.sk_words + kSkFlags + 4 * blockIdx.x + warp, epoch1);
+                if (lane == 0) st_release_u32(args.sk_words + kSkFlags + kSkFlagsPerCta * blockIdx.x + warp, epoch1);
                 continue;
             }
             if (V::STREAMK != 0 && epi_ok && c0 > 0) {
@@ -702,7 +699,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     const int64_t lo_j = (int64_t)j * W_sk / G, hi_j = ((int64_t)j + 1) * W_sk / G;
                     if (hi_j <= tile_lo) break;
                     if (lo_j == hi_j) continue;  // an empty range contributes nothing
-                    const unsigned *flag = args.sk_words + kSkFlags + 4 * j + warp;
+                    const unsigned *flag = args.sk_words + kSkFlags + kSkFlagsPerCta * j + warp;
                     const uint64_t t0 = globaltimer_ns();
                     bool ready = false;
                     while (!(ready = ld_acquire_u32(flag) == epoch1 + args.sk_wait_bias)) {
@@ -730,13 +727,14 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 float *stg = reinterpret_cast<float *>(smem_raw + (sbase - raw) + V::STG_OFFSET) +
                              warp * V::STG_WARP_FLOATS;
                 const int rr = lane >> 3, cc = (lane & 7) * 4;
+                const float as = alpha;
 #pragma unroll
                 for (int jb = 0; jb < COLS; jb += 32) {
 #pragma unroll
                     for (int q = 0; q < 32; q += 4)
                         *reinterpret_cast<float4 *>(stg + lane * V::STG_LD + q) =
-                            make_float4(alpha * racc[jb + q], alpha * racc[jb + q + 1], alpha * racc[jb + q + 2],
-                                        alpha * racc[jb + q + 3]);
+                            make_float4(as * racc[jb + q], as * racc[jb + q + 1], as * racc[jb + q + 2],
+                                        as * racc[jb + q + 3]);
                     __syncwarp();
                     const int col = n0 + grp * COLS + jb + cc;
 #pragma unroll
@@ -770,11 +768,12 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 if (row < args.M && cbase < args.N) {
                     float *cp = args.C + (int64_t)row * args.ldc + cbase;
                     const int ncol = args.N - cbase;
+                    const float as = alpha;
                     if (ncol >= COLS && args.vec4) {
 #pragma unroll
                         for (int q = 0; q < COLS; q += 4) {
-                            float4 v = make_float4(alpha * racc[q], alpha * racc[q + 1], alpha * racc[q + 2],
-                                                   alpha * racc[q + 3]);
+                            float4 v = make_float4(as * racc[q], as * racc[q + 1], as * racc[q + 2],
+                                                   as * racc[q + 3]);
                             if (beta != 0.f) {
                                 const float4 o = *reinterpret_cast<const float4 *>(cp + q);
                                 v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
@@ -785,7 +784,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
 #pragma unroll
                         for (int q = 0; q < COLS; ++q) {
                             if (q < ncol) {
-                                const float v = alpha * racc[q];
+                                const float v = as * racc[q];
                                 cp[q] = (beta != 0.f) ? v + beta * cp[q] : v;
                             }
                         }

@@ -105,44 +105,47 @@ def test_rank1_operands_closed_form_and_planes(K):
 
 
 def test_f16_chunk_scales_hand_values():
-    X = np.zeros((4, 300))
+    X = np.zeros((5, 300))
     X[0, 5] = 1.0            # max 1: 2^14 * 1 in [2^14, 2^15)
     X[1, 0] = 3.0            # floor(log2 3) = 1 -> S = 13, 3 * 2^13 = 24576
-    X[2, 130] = -2.0 ** -60  # below the clamp: S = 63 in chunk 1
-    X[3, 299] = 2.0 ** 90    # above: S = -63 in chunk 2
+    X[1, 299] = -2.0         # another chunk: S = 13 there as well
+    X[2, 130] = -2.0 ** -60  # below the clamp: S = 63
+    X[3, 299] = 2.0 ** 90    # above: S = -63
     S = f16_chunk_scales(X)
-    assert S.shape == (4, 3)
-    assert S[0, 0] == 14 and S[1, 0] == 13 and S[2, 1] == 63 and S[3, 2] == -63
-    assert S[0, 1] == 63     # an all-zero chunk
+    assert S.shape == (5, 3)
+    assert S[0, 0] == 14 and S[1, 0] == 13 and S[1, 2] == 13 and S[2, 1] == 63 and S[3, 2] == -63
+    assert S[0, 1] == 63 and S[4, 0] == 63     # all-zero chunks
+    G = f16_chunk_scales(X, group=32)          # one group of all five rows
+    assert G.shape == (1, 3) and G[0, 0] == 13 and G[0, 2] == -63
     h0, h1, _ = f16x2_planes_scaled(X)
-    assert h0[1, 0] == 24576.0 and h1[1, 0] == 0.0
+    assert h0[1, 0] == 24576.0 and h1[1, 0] == 0.0 and h0[1, 299] == -16384.0
     assert np.isinf(h0[3, 299])   # 2^90 * 2^-63 = 2^27 overflows FP16: outside the range
 
 
 @pytest.mark.parametrize("kind", ["uniform", "logu", "normal"])
-def test_f16_scaled_planes_error_bound(kind):
-    X = matrix(kind, 9, 16, 1000)
-    h0, h1, S = f16x2_planes_scaled(X)
-    back = np.ldexp(h0 + h1, -np.repeat(S, 128, axis=1)[:, :1000])
-    # two 11-bit planes: error below 2^-22 of the value plus FP16 subnormal
-    # spacing (2^-24 of the scaled unit) relative to the chunk
+@pytest.mark.parametrize("group", [1, 32])
+def test_f16_scaled_planes_error_bound(kind, group):
+    X = matrix(kind, 9, 64, 1000)
+    h0, h1, E = f16x2_planes_scaled(X, group)
+    back = np.ldexp(h0 + h1, -E)
+    # two 11-bit planes: error below 2^-21 of the value, plus half the FP16
+    # subnormal spacing (2^-25 of the scaled unit) for values far below the
+    # maximum of their group's chunk
     err = np.abs(X.astype(np.float64) - back)
-    assert np.all(err <= np.abs(X) * 2.0 ** -21 + np.ldexp(2.0 ** -25, -np.repeat(S, 128, axis=1)[:, :1000]))
+    assert np.all(err <= np.abs(X) * 2.0 ** -21 + np.ldexp(2.0 ** -25, -E))
     assert np.all(np.abs(h0) <= 2 ** 15)   # rounding may reach 2^15; FP16 holds up to 65504
 
 
 @pytest.mark.parametrize("M,N,K", [(300, 200, 1024), (300, 136, 4096)])
 def test_wide_int_operands_under_the_scaled_f16_split(M, N, K):
-    # The same input sets are exact for 3xF16: A's rows and B's columns (B^T's
-    # rows) split into two planes with nothing lost, the product h1 h1 is
-    # always zero, and the three kept products are each non-zero somewhere.
+    # The same input sets are exact for 3xF16: A's rows and B's column groups
+    # split into two planes with nothing lost, the product h1 h1 is always
+    # zero, and the three kept products are each non-zero for many outputs.
     A, B, _ = wide_int_operands(7, M, N, K)
-    a0, a1, Sa = f16x2_planes_scaled(A)
-    b0, b1, Sb = f16x2_planes_scaled(B.T)
-    ka = np.repeat(Sa, 128, axis=1)[:, :K]
-    kb = np.repeat(Sb, 128, axis=1)[:, :K]
-    assert np.array_equal(np.ldexp(a0 + a1, -ka), A.astype(np.float64))
-    assert np.array_equal(np.ldexp(b0 + b1, -kb), B.T.astype(np.float64))
+    a0, a1, Ea = f16x2_planes_scaled(A)
+    b0, b1, Eb = f16x2_planes_scaled(B.T, group=32)
+    assert np.array_equal(np.ldexp(a0 + a1, -Ea), A.astype(np.float64))
+    assert np.array_equal(np.ldexp(b0 + b1, -Eb), B.T.astype(np.float64))
     assert not (np.abs(a1) @ np.abs(b1).T).any()
     for pa, pb in ((a0, b0), (a0, b1), (a1, b0)):
         assert (np.abs(pa) @ np.abs(pb).T > 0).mean() > 0.25
