@@ -255,13 +255,15 @@ int pt_selected_variant(char transA, char transB, int64_t M, int64_t N, int64_t 
                         const float *A, int64_t lda, const float *B, int64_t ldb,
                         const float *C, int64_t ldc);
 
-/* ---- grouped SGEMM: many independent problems in one persistent launch ----
+/* ---- grouped SGEMM: many independent problems in a few persistent launches ---
  * (The paper tunes single GEMM calls; this batches uneven problems, each
  * with its own variant choice.)  One descriptor per problem; same operation
  * and conventions as pt_sgemm per problem.  `tile` is the problem's tile
- * configuration in the grouped kernel (0: 64x64, 1: 128x64, 2: 128x128 with
- * 16-byte aligned A, B, C and leading dimensions divisible by 4; 3: 64x64
- * for any alignment); pt_grouped_plan fills it from the runtime selector. */
+ * configuration: 0: 64x64, 1: 128x64, 2: 128x128 SIMT tiles with 16-byte
+ * aligned A, B, C and leading dimensions divisible by 4; 3: 64x64 SIMT for
+ * any alignment; 4 (PT_GROUPED_TILE_TC): 128x128 scaled 3xF16 tensor-core
+ * tile, any alignment, K > 0.  pt_grouped_plan fills it from the runtime
+ * selector. */
 typedef struct pt_gemm_problem {
     int64_t m, n, k;
     const float *A;
@@ -277,18 +279,24 @@ typedef struct pt_gemm_problem {
 } pt_gemm_problem_t;
 
 #define PT_GROUPED_MAX 4096  /* problems per pt_sgemm_grouped call */
+#define PT_GROUPED_TILE_TC 4 /* tile value: 128 x 128 scaled 3xF16 tensor-core tile */
 
 /* Sets problems[i].tile for every problem (host array): the variant the
  * loaded manifest's selector picks for that shape (see pt_sgemm) mapped to
- * the grouped tile of the nearest area (tensor-core picks -> 128x128); 3
- * when the problem's operands are not 16-byte aligned. */
+ * the grouped tile of the nearest area, or to PT_GROUPED_TILE_TC when the
+ * pick is a tensor-core version and K > 0; 3 when the problem's operands are
+ * not 16-byte aligned. */
 int pt_grouped_plan(pt_gemm_problem_t *problems, int count);
 
-/* Runs `count` problems in one launch of a persistent kernel (a grid of
- * resident CTAs walking all problems' tiles).  `problems` (host) is validated;
- * `problems_dev` must be a device copy of the same array, caller-owned, left
- * unchanged until the launch has completed.  Asynchronous on `stream`; no
- * workspace and no allocation. */
+/* Runs `count` problems: the SIMT tiles in one launch of a persistent kernel
+ * (a grid of resident CTAs walking all their tiles); problems with the
+ * tensor-core tile through a plan kernel, one split kernel and one
+ * persistent tensor-core kernel, whose planes live in the stream's library
+ * workspace (see pt_shutdown; it grows only outside stream capture, so make
+ * a first call on the stream before capturing one).  `problems` (host) is
+ * validated; `problems_dev` must be a device copy of the same array,
+ * caller-owned, left unchanged until the launches have completed (for a
+ * captured graph: while it is replayed).  Asynchronous on `stream`. */
 int pt_sgemm_grouped(const pt_gemm_problem_t *problems, const pt_gemm_problem_t *problems_dev, int count,
                      void *stream);
 

@@ -53,7 +53,7 @@ def _gen_module():
 def _sources():
     _gen_module().generate(GEN)
     cu = sorted(glob.glob(os.path.join(GEN, "variants_*.cu")))
-    cu += [os.path.join(CSRC, f) for f in ("registry.cu", "api.cu", "tuner.cu", "tc.cu", "noalloc.cu", "grouped.cu")]
+    cu += [os.path.join(CSRC, f) for f in ("registry.cu", "api.cu", "tuner.cu", "tc.cu", "noalloc.cu", "grouped.cu", "grouped_tc.cu")]
     cpp = [os.path.join(CSRC, "select.cpp")]
     return cu, cpp
 

@@ -1,4 +1,5 @@
-// Persistent grouped SGEMM: many independent problems in one launch.
+// Persistent grouped SGEMM: many independent problems in one launch (SIMT
+// tiles; problems given the tensor-core tile run in grouped_tc.cu).
 //
 // Each problem carries a tile configuration chosen on the host by the runtime
 // selector (pt_grouped_plan maps the variant the loaded manifest picks for
@@ -15,6 +16,7 @@
 #include <cstring>
 
 #include "common.h"
+#include "grouped_tc.cuh"
 #include "launch.cuh"
 
 namespace pt {
@@ -137,8 +139,11 @@ int check_problem(const pt_gemm_problem_t &p, int i) {
     if (p.m > 0 && p.n > 0) {
         if (!p.C) return set_error(PT_EINVAL, 1, "problem %d: C is NULL", i);
         if (p.k > 0 && (!p.A || !p.B)) return set_error(PT_EINVAL, 1, "problem %d: A or B is NULL", i);
-        if (p.tile < 0 || p.tile > 3) return set_error(PT_EINVAL, 1, "problem %d: tile %d (call pt_grouped_plan)", i, p.tile);
-        if (p.tile != 3) {
+        if (p.tile < 0 || p.tile > PT_GROUPED_TILE_TC)
+            return set_error(PT_EINVAL, 1, "problem %d: tile %d (call pt_grouped_plan)", i, p.tile);
+        if (p.tile == PT_GROUPED_TILE_TC && p.k == 0)
+            return set_error(PT_EINVAL, 1, "problem %d: the tensor-core tile needs K > 0", i);
+        if (p.tile < 3) {
             const bool al = (reinterpret_cast<uintptr_t>(p.C) % 16 == 0) && p.ldc % 4 == 0 &&
                             (p.k == 0 || ((reinterpret_cast<uintptr_t>(p.A) % 16 == 0) && p.lda % 4 == 0 &&
                                           (reinterpret_cast<uintptr_t>(p.B) % 16 == 0) && p.ldb % 4 == 0));
@@ -178,7 +183,8 @@ int pt_grouped_plan(pt_gemm_problem_t *problems, int count) {
         }
         const pt_variant_desc_t &d = tab[v].desc;
         const int area = d.bm * d.bn;
-        p.tile = (d.kind != 0 || area >= 128 * 128) ? 2 : (area >= 128 * 64 ? 1 : 0);
+        if (d.kind != 0 && p.k > 0) p.tile = PT_GROUPED_TILE_TC;  // tensor-core pick: the 3xF16 tile
+        else p.tile = area >= 128 * 128 ? 2 : (area >= 128 * 64 ? 1 : 0);
     }
     return PT_OK;
 }
@@ -194,13 +200,17 @@ int pt_sgemm_grouped(const pt_gemm_problem_t *problems, const pt_gemm_problem_t 
     for (int i = 0; i < count; ++i) {
         const int rc = check_problem(problems[i], i);
         if (rc != PT_OK) return rc;
-        if (problems[i].m > 0 && problems[i].n > 0) {
+        if (problems[i].m > 0 && problems[i].n > 0 && problems[i].tile != PT_GROUPED_TILE_TC) {
             int bm, bn;
             tile_dims(problems[i].tile, &bm, &bn);
             tiles += ((problems[i].m + bm - 1) / bm) * ((problems[i].n + bn - 1) / bn);
         }
     }
     if (tiles > 0x7fffffff) return set_error(PT_EUNSUPPORTED, 1, "too many tiles");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Tensor-core problems: plan, split and one persistent tensor-core kernel.
+    int rc = grouped_tc_launch(problems, problems_dev, count, st);
+    if (rc != PT_OK) return rc;
     if (tiles == 0) return PT_OK;
     const int dev = current_device();
     const uint64_t bit = 1ull << (dev & 63);
@@ -215,7 +225,6 @@ int pt_sgemm_grouped(const pt_gemm_problem_t *problems, const pt_gemm_problem_t 
     if (sms <= 0) sms = 1;
     if (per_sm <= 0) per_sm = 1;
     const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, tiles);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     grouped_sgemm_kernel<<<(unsigned)grid, kThreads, kSmem, st>>>(problems_dev, count, nullptr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PT_OK : set_error(PT_ECUDA, 0, "grouped kernel: %s", cudaGetErrorString(e));

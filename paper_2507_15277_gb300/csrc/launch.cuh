@@ -32,6 +32,12 @@ int current_device();
 // looking it up allocates nothing; NULL if the lookup fails.
 int *err_word(int dev);
 
+// The library's workspace of (current device, stream) with at least `need`
+// bytes (tc.cu): its first kSkHeaderBytes hold the stream-K header.  Grown
+// outside stream capture only (PT_EUNSUPPORTED while capturing); `dry`
+// checks without allocating.
+int stream_workspace(cudaStream_t st, size_t need, bool dry, void **out);
+
 // Stream-K finisher wait settings for the next launches (api.cu,
 // pt_debug_streamk_wait): time limit in ns and the awaited-value offset.
 void streamk_wait_settings(uint64_t *limit_ns, unsigned *bias);

@@ -96,6 +96,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// 1-D bulk copy of `bytes` contiguous bytes (a multiple of 16; both addresses
+// 16-byte aligned) from global memory into this CTA's shared memory,
+// completing on the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
 // Orders this thread's generic-proxy shared-memory writes before later
 // async-proxy accesses (TMA, tensor-core operand reads) of the same data.
 __device__ __forceinline__ void fence_proxy_async_smem() {

@@ -244,6 +244,8 @@ VariantEntry tc_entry(const char *name) {
 
 }  // namespace
 
+int stream_workspace(cudaStream_t st, size_t need, bool dry, void **out) { return workspace(st, need, dry, out); }
+
 // Tensor-core variants appended to the registry after the SIMT family.
 std::vector<VariantEntry> tc_variants() {
     return {
