@@ -134,11 +134,11 @@ int pt_variant_by_name(const char *name);
  * divisible by 4, and return PT_EUNSUPPORTED otherwise.
  * 3xTF32 (Markidis et al.-style split x = hi + lo, three products), BF16x3
  * (x = b0 + b1 + b2, six products) and scaled 3xF16 give FP32-level error.
- * 3xF16 ("tc3xf16_" names) multiplies, per 128 values of k, each row of
+ * 3xF16 ("tc3xf16_" names) multiplies, per 256 values of k, each row of
  * op(A) and each group of 32 consecutive columns of op(B) by a power of two
  * that brings its largest magnitude there into [2^14, 2^15), splits into two
  * FP16 planes (11-bit significands, as TF32) and undoes the scales on each
- * 128-k partial product: three MMAs at the FP16 rate, error relative to the
+ * 256-k partial product: three MMAs at the FP16 rate, error relative to the
  * largest |a| of the row times the largest |b| of the column's group.  It
  * gives that accuracy while those maxima lie in [2^-49, 2^78]; larger values
  * overflow FP16 (C gets Inf or

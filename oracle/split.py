@@ -10,7 +10,7 @@ planes and drop the smallest cross products:
           b2 = RN_bf16(x - b0 - b1);
           a*b ~ sum of a_i*b_j over i + j <= 2       (a1b2, a2b1, a2b2 dropped)
 
-  3xF16 (scaled): k is cut into chunks of 128 values; chunk c of row i of
+  3xF16 (scaled): k is cut into chunks of 256 values; chunk c of row i of
           op(A) is multiplied by 2^S with S = 14 - floor(log2 m), m its
           largest magnitude, clamped to [-63, 63] (63 when m = 0); chunk c of
           a group of 32 consecutive columns of op(B) likewise, m over the
@@ -61,7 +61,7 @@ def bf16x3_planes(x):
     return b0, b1, b2
 
 
-def f16_chunk_scales(X, group: int = 1, chunk: int = 128) -> np.ndarray:
+def f16_chunk_scales(X, group: int = 1, chunk: int = 256) -> np.ndarray:
     """Exponents S[g, c] of the 3xF16 split of X (rows x K), for groups of
     `group` consecutive rows (1 for op(A); 32 for the rows of op(B)^T) and
     chunks of `chunk` values of k: 2^S brings the largest magnitude of the
@@ -77,7 +77,7 @@ def f16_chunk_scales(X, group: int = 1, chunk: int = 128) -> np.ndarray:
     return S
 
 
-def f16x2_planes_scaled(X, group: int = 1, chunk: int = 128):
+def f16x2_planes_scaled(X, group: int = 1, chunk: int = 256):
     """(h0, h1, E) of the scaled 3xF16 split of the rows of X: h0 + h1 is
     X[r, k] * 2^E[r, k] on the FP16 grid (FP64 arrays), E[r, k] the scale
     exponent of r's group and k's chunk."""

@@ -1,6 +1,6 @@
 // Split kernel of the tensor-core versions: FP32 operands to K-major
 // low-precision planes (3xTF32: hi, lo; BF16x3: b0, b1, b2; scaled 3xF16:
-// h0, h1 of the value times a power-of-two scale per 128 values of k)
+// h0, h1 of the value times a power-of-two scale per 256 values of k)
 // in a workspace that the GEMM kernel reads through TMA.
 #pragma once
 
@@ -15,7 +15,7 @@ constexpr int kTcTf32 = 0;
 constexpr int kTcBf16x3 = 1;
 constexpr int kTcF16s = 2;  // scaled FP16 split, three products (3xTF32's precision, FP16 rate)
 
-// Scaled FP16 split: k is cut into chunks of 128 values.  Chunk c of row r of
+// Scaled FP16 split: k is cut into chunks of 256 values.  Chunk c of row r of
 // op(A) is multiplied by 2^S_A(r, c); chunk c of a group of 32 consecutive
 // columns g of op(B) (32 consecutive rows of the K-major B planes) by
 // 2^S_B(g, c).  S = 14 - floor(log2 m), m the largest magnitude in that
@@ -224,7 +224,7 @@ template <int KIND>
 __global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, const SplitOperand b, int K,
                                                        int64_t pitch, int ya) {
     __shared__ float tile[SPLIT_KT][64][33];
-    __shared__ float gmax[SPLIT_KT / 2][8];
+    __shared__ float gmax[8];
     const bool first = (int)blockIdx.y < ya;
     const SplitOperand &o = first ? a : b;
     const int by = first ? (int)blockIdx.y : (int)blockIdx.y - ya;
@@ -237,52 +237,35 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, con
     pdl_wait();
     split_load_block(o, K, r0, kb, tid, x, tile);
     if constexpr (KIND == kTcF16s) {
-        // Slabs 2c and 2c + 1 form chunk kb / 128 + c.  First operand: the
-        // maximum of each row's chunk (its eight threads are consecutive
+        // The block's 256 values of k are chunk blockIdx.x.  First operand:
+        // the maximum of each row's chunk (its eight threads are consecutive
         // lanes); second operand: of the block's 32 rows (all threads).
-        static_assert(SPLIT_KT % 2 == 0, "a block covers whole 128-k chunks");
+        static_assert(SPLIT_K_PER_BLOCK == 256, "a block covers one 256-k chunk");
+        float m = 0.f;
 #pragma unroll
-        for (int c = 0; c < SPLIT_KT / 2; ++c) {
-            float m = 0.f;
+        for (int t = 0; t < SPLIT_KT; ++t)
 #pragma unroll
-            for (int t = 2 * c; t < 2 * c + 2; ++t)
+            for (int i = 0; i < 8; ++i) m = fmaxf(m, fabsf(x[t][i]));
 #pragma unroll
-                for (int i = 0; i < 8; ++i) m = fmaxf(m, fabsf(x[t][i]));
-#pragma unroll
-            for (int off = 1; off < 8; off <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-            if (!first) {
-                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
-                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
-                if ((tid & 31) == 0) gmax[c][tid >> 5] = m;
-            }
-            if (first) {
-                const int S = f16_scale_exp(m);
-                const float sc = pow2f(S);
-#pragma unroll
-                for (int t = 2 * c; t < 2 * c + 2; ++t)
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) x[t][i] *= sc;
-                const int gc = kb / 128 + c;
-                if ((tid & 7) == 0 && r < o.rows && 128 * gc < pitch) o.scale[(int64_t)gc * o.ld_scale + r] = pow2f(-S);
-            }
-        }
+        for (int off = 1; off < 8; off <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
         if (!first) {
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+            if ((tid & 31) == 0) gmax[tid >> 5] = m;
             __syncthreads();
+            m = gmax[0];
 #pragma unroll
-            for (int c = 0; c < SPLIT_KT / 2; ++c) {
-                float m = gmax[c][0];
-#pragma unroll
-                for (int w = 1; w < 8; ++w) m = fmaxf(m, gmax[c][w]);
-                const int S = f16_scale_exp(m);
-                const float sc = pow2f(S);
-#pragma unroll
-                for (int t = 2 * c; t < 2 * c + 2; ++t)
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) x[t][i] *= sc;
-                const int gc = kb / 128 + c;
-                if (tid == 0 && 128 * gc < pitch) o.scale[(int64_t)gc * o.ld_scale + by] = pow2f(-S);
-            }
+            for (int w = 1; w < 8; ++w) m = fmaxf(m, gmax[w]);
         }
+        const int S = f16_scale_exp(m);
+        const float sc = pow2f(S);
+#pragma unroll
+        for (int t = 0; t < SPLIT_KT; ++t)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[t][i] *= sc;
+        const int gc = (int)blockIdx.x;
+        if (first && (tid & 7) == 0 && r < o.rows) o.scale[(int64_t)gc * o.ld_scale + r] = pow2f(-S);
+        if (!first && tid == 0) o.scale[(int64_t)gc * o.ld_scale + by] = pow2f(-S);
     }
 #pragma unroll
     for (int t = 0; t < SPLIT_KT; ++t) {

@@ -118,7 +118,7 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     // of op(B) 32-column groups, [chunk][round_up(N, 128) / 32].
     const int64_t header = align256((int64_t)kSkHeaderBytes);
     const int64_t partials = V::STREAMK ? align256(grid * V::BM * V::BN * 4) : 0;
-    const int64_t nchk = ((int64_t)a.K + 127) / 128;
+    const int64_t nchk = ((int64_t)a.K + V::CHUNK_K - 1) / V::CHUNK_K;
     const int64_t ld_sa = ((int64_t)a.M + 127) / 128 * 128, ld_sb = ((int64_t)a.N + 127) / 128 * 4;
     const int64_t sa_bytes = V::SCALED ? align256(nchk * ld_sa * 4) : 0;
     const int64_t sb_bytes = V::SCALED ? align256(nchk * ld_sb * 4) : 0;

@@ -8,11 +8,11 @@
 //   BF16x3:  x = b0 + b1 + b2, b0 = RN_bf16(x), b1 = RN_bf16(x - b0),
 //            b2 = RN_bf16(x - b0 - b1);
 //            a*b ~ sum of the six b_i*b_j with i + j <= 2 (kind::f16 with BF16, 6 MMAs)
-//   3xF16:   x' = x * 2^S (S per 128 values of k and row of op(A), or group
+//   3xF16:   x' = x * 2^S (S per 256 values of k and row of op(A), or group
 //            of 32 columns of op(B), so that the largest |x'| there is in
 //            [2^14, 2^15)), x' = h0 + h1 on the FP16 grid (11-bit
 //            significands, as TF32); a'*b' ~ h0 h0 + h0 h1 + h1 h0 (kind::f16
-//            with F16, 3 MMAs at the BF16 rate); each 128-k partial product is
+//            with F16, 3 MMAs at the BF16 rate); each 256-k partial product is
 //            multiplied by 2^-S_A * 2^-S_B when it is drained.
 // The dropped terms are O(2^-22) (3xTF32, 3xF16) and O(2^-24) (BF16x3)
 // relative to |a*b| (3xF16: relative to the largest |a| of the row's chunk
@@ -98,9 +98,13 @@ struct Tc {
     // MMA instructions per k step after pairing along N (see tc_op).
     static constexpr int NOPS = KIND == kTcBf16x3 ? 4 : 2;
     // Promotion: the tensor-core accumulator is restarted every CHUNK_KT
-    // k-tiles (128 values of k) and added into FP32 registers with IEEE
-    // round-to-nearest, so the accumulation error grows with 128, not K.
-    static constexpr int CHUNK_KT = 128 / BK;
+    // k-tiles (CHUNK_K values of k) and added into FP32 registers with IEEE
+    // round-to-nearest, so the accumulation error grows with CHUNK_K, not K.
+    // 3xF16 drains every 256 values of k (its scales' chunk): its MMAs run at
+    // twice the rate per k of the other kinds, so a 128-k chunk would leave
+    // the epilogue half the time per drain.
+    static constexpr int CHUNK_K = SCALED ? 256 : 128;
+    static constexpr int CHUNK_KT = CHUNK_K / BK;
     static constexpr int A_PLANE_BYTES = BM * SWZ;
     static constexpr int B_PLANE_BYTES = BN * SWZ;
     // FP32 tile of the fused operand: B as [BK][BN], A as [BM][BK].
@@ -216,7 +220,7 @@ struct TcArgs {
     // CTA b's partial tile (partials + b * BM * BN, row-major BM x BN).
     unsigned *sk_words;
     float *sk_partials;
-    // 3xF16: 2^-S of chunk c (128 values of k) of row r of op(A) at
+    // 3xF16: 2^-S of chunk c (256 values of k) of row r of op(A) at
     // scale_a[c * ld_sa + r] (ld_sa >= round_up(M, 128)), and of the 32-column
     // group g of op(B) at scale_b[c * ld_sb + g] (ld_sb >= round_up(N, 128) / 32).
     const float *scale_a;

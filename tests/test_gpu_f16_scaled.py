@@ -1,7 +1,7 @@
 """GPU: the scaled 3xF16 tensor-core versions on inputs whose magnitudes
 differ by row, by column and along k.
 
-Per 128 values of k, each row of op(A) and each group of 32 consecutive
+Per 256 values of k, each row of op(A) and each group of 32 consecutive
 columns of op(B) is scaled by a power of two before the FP16 split, so the
 error of C_ij is bounded by the magnitudes in row i of A and in the 32-column
 group of j in B, not by the largest entries of the matrices.  The test holds

@@ -105,21 +105,21 @@ def test_rank1_operands_closed_form_and_planes(K):
 
 
 def test_f16_chunk_scales_hand_values():
-    X = np.zeros((5, 300))
+    X = np.zeros((5, 600))
     X[0, 5] = 1.0            # max 1: 2^14 * 1 in [2^14, 2^15)
     X[1, 0] = 3.0            # floor(log2 3) = 1 -> S = 13, 3 * 2^13 = 24576
-    X[1, 299] = -2.0         # another chunk: S = 13 there as well
-    X[2, 130] = -2.0 ** -60  # below the clamp: S = 63
-    X[3, 299] = 2.0 ** 90    # above: S = -63
-    S = f16_chunk_scales(X)
+    X[1, 599] = -2.0         # another chunk: S = 13 there as well
+    X[2, 300] = -2.0 ** -60  # below the clamp: S = 63
+    X[3, 599] = 2.0 ** 90    # above: S = -63
+    S = f16_chunk_scales(X)  # chunks of 256 values of k
     assert S.shape == (5, 3)
     assert S[0, 0] == 14 and S[1, 0] == 13 and S[1, 2] == 13 and S[2, 1] == 63 and S[3, 2] == -63
     assert S[0, 1] == 63 and S[4, 0] == 63     # all-zero chunks
     G = f16_chunk_scales(X, group=32)          # one group of all five rows
     assert G.shape == (1, 3) and G[0, 0] == 13 and G[0, 2] == -63
     h0, h1, _ = f16x2_planes_scaled(X)
-    assert h0[1, 0] == 24576.0 and h1[1, 0] == 0.0 and h0[1, 299] == -16384.0
-    assert np.isinf(h0[3, 299])   # 2^90 * 2^-63 = 2^27 overflows FP16: outside the range
+    assert h0[1, 0] == 24576.0 and h1[1, 0] == 0.0 and h0[1, 599] == -16384.0
+    assert np.isinf(h0[3, 599])   # 2^90 * 2^-63 = 2^27 overflows FP16: outside the range
 
 
 @pytest.mark.parametrize("kind", ["uniform", "logu", "normal"])
