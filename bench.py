@@ -669,6 +669,31 @@ def per_shape_times(calls, stream, reps=3):
     return [statistics.median(x) for x in times], method
 
 
+def per_shape_stream_times(calls, stream, repeat=10):
+    """Device time of each call when it runs back to back with itself:
+    `repeat` launches of the call between two timing events, all shapes in
+    one captured graph replayed once (after one warm replay).  Launch
+    overlap is then as in the timed step, but the shape's inputs are in L2
+    after its first launch.  Returns per-call ms (total / repeat)."""
+    import torch
+    n = len(calls)
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n + 1)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            ev[0].record(stream)
+            for i, c in enumerate(calls):
+                for _ in range(repeat):
+                    c()
+                ev[i + 1].record(stream)
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+    out = [ev[i].elapsed_time(ev[i + 1]) / repeat for i in range(n)]
+    del g
+    return out
+
+
 def cpu_oracle_sample(shapes, rows_per_shape, seed_base=1000):
     """Times the FP64 CPU oracle on the first `rows_per_shape` rows of every
     shape (all rows when M is smaller).  Returns (TFLOP/s, seconds, cores, flops)."""
@@ -956,6 +981,12 @@ def main():
     shape_ms, per_shape_timing = per_shape_times(
         [lambda i=i: pt.sgemm(devA[i], devB[i], devC[i], stream=stream) for i in range(len(shapes))], stream)
 
+    try:
+        shape_ms_stream = per_shape_stream_times(
+            [lambda i=i: pt.sgemm(devA[i], devB[i], devC[i], stream=stream) for i in range(len(shapes))], stream)
+    except (RuntimeError, TypeError):
+        shape_ms_stream = [None] * len(shapes)
+
     # ---- timed region: graph replays ----
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -1240,13 +1271,16 @@ def main():
         "kappa": sel.get(args.k, {}).get("names"),
         "selectors": info.get("selectors"),
         "tuning": {"tune_s": info.get("tune_s"), "select_s": info.get("select_s"), "table": table},
-        "per_shape": [dict({"shape": list(s), "ms": round(ms, 5), "tflops": round(f / (ms * 1e-3) / 1e12, 3),
+        "per_shape": [dict({"shape": list(s), "ms": round(ms, 5), "ms_stream": None if msb is None else round(msb, 5),
+                            "tflops": round(f / (ms * 1e-3) / 1e12, 3),
                             "gbs": round(4.0 * (s[0] * s[2] + s[2] * s[1] + s[0] * s[1]) / (ms * 1e-3) / 1e9, 1),
                             "variant": pt.variant(p)["name"], "cublas_tflops": round(f / (cm * 1e-3) / 1e12, 3)},
                            **fracs(p, f / (ms * 1e-3) / 1e12))
-                      for s, ms, f, p, cm in zip(shapes, shape_ms, flops, picks, cub_ms)],
+                      for s, ms, msb, f, p, cm in zip(shapes, shape_ms, shape_ms_stream, flops, picks, cub_ms)],
         "small_shapes": {"count": len(small), "max_gflop": 1.1, "sum_ms": sum(shape_ms[i] for i in small),
-                         "sum_ms_all": sum(shape_ms)},
+                         "sum_ms_all": sum(shape_ms),
+                         "sum_ms_stream": (sum(shape_ms_stream[i] for i in small)
+                                           if shape_ms_stream[0] is not None else None)},
         "config1": {"workload": "256^3 NN, alpha=1, beta=0, U[-1,1], fixed 128x128x8 variant", "variant": c1_name,
                     "ms": c1_ms, "tflops": 2.0 * 256 ** 3 / (c1_ms * 1e-3) / 1e12,
                     "frac_fp32_peak": 2.0 * 256 ** 3 / (c1_ms * 1e-3) / 1e12 / fp32_peak},

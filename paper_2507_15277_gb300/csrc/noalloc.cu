@@ -167,8 +167,21 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     const SplitOperand ob{B, ldb, tb ? 0 : 1, (int)N, wB, b_plane, vb};
     const int ya = (int)((M + 31) / 32), yb = (int)((N + 31) / 32);
     const dim3 sgrid((unsigned)((pitch + SPLIT_K_PER_BLOCK - 1) / SPLIT_K_PER_BLOCK), (unsigned)(ya + yb));
-    tc_split_kernel<kTcTf32><<<sgrid, 256, 0, st>>>(oa, ob, (int)K, pitch, ya);
-    cudaError_t e = cudaGetLastError();
+    // Both kernels are launched with programmatic stream serialization, as the
+    // registry's versions are: each waits (griddepcontrol.wait) for the
+    // previous kernel of the stream before touching global memory, and its
+    // launch and prologue overlap that kernel's tail.
+    cudaLaunchAttribute pdl[1];
+    unsigned npdl = 0;
+    add_pdl_attr(pdl, npdl);
+    cudaLaunchConfig_t scfg;
+    std::memset(&scfg, 0, sizeof(scfg));
+    scfg.gridDim = sgrid;
+    scfg.blockDim = dim3(256, 1, 1);
+    scfg.stream = st;
+    scfg.attrs = pdl;
+    scfg.numAttrs = npdl;
+    cudaError_t e = cudaLaunchKernelEx(&scfg, tc_split_kernel<kTcTf32>, oa, ob, (int)K, pitch, ya);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 
     CUtensorMap mA, mB;
@@ -199,8 +212,15 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     // next tile while the epilogue drains the previous one.
     const int64_t tiles = ((N + NoAllocCfg::BN - 1) / NoAllocCfg::BN) * ((M + NoAllocCfg::BM - 1) / NoAllocCfg::BM);
     const dim3 grid((unsigned)(tiles < sms ? tiles : sms));
-    tc_sgemm_kernel<NoAllocCfg><<<grid, NoAllocCfg::THREADS, NoAllocCfg::SMEM_BYTES, st>>>(t, mA, mB);
-    e = cudaGetLastError();
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NoAllocCfg::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = NoAllocCfg::SMEM_BYTES;
+    cfg.stream = st;
+    cfg.attrs = pdl;
+    cfg.numAttrs = npdl;
+    e = cudaLaunchKernelEx(&cfg, tc_sgemm_kernel<NoAllocCfg>, t, mA, mB);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "tensor-core kernel: %s", cudaGetErrorString(e));
     return PT_OK;
 }
