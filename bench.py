@@ -1252,8 +1252,10 @@ def main():
                               "splits with FP32 accumulation",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "clocks": clk,
-        # per call: SIMT one kernel; split + GEMM; 3xF16 row maxima + split + GEMM
-        "gpu_launches": args.steps * sum({0: 1, 3: 3}.get(pt.variant(p)["kind"], 2) for p in picks),
+        # per call: SIMT or both operands split in the GEMM kernel: one kernel;
+        # otherwise the split kernel and the GEMM kernel
+        "gpu_launches": args.steps * sum(1 if pt.variant(p)["kind"] == 0 or "_fab" in pt.variant(p)["name"] else 2
+                                         for p in picks),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "wall_s": e2e_wall, "ms_per_step": e2e_ms / args.steps,
                 "h2d_gbs_alone": h2d / (h2d_ms * 1e-3) / 1e9, "d2h_gbs_alone": d2h / (d2h_ms * 1e-3) / 1e9,

@@ -158,8 +158,11 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     add_pdl_attr(sattr, nsattr);
     scfg.attrs = sattr;
     scfg.numAttrs = nsattr;
-    cudaError_t e = V::FUSEA ? cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, ob, ob, (int)a.K, pitch, ya)
-                             : cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, oa, ob, (int)a.K, pitch, ya);
+    cudaError_t e = cudaSuccess;
+    if constexpr (V::FUSE != 3) {  // both operands fused: no split kernel at all
+        e = V::FUSEA ? cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, ob, ob, (int)a.K, pitch, ya)
+                     : cudaLaunchKernelEx(&scfg, tc_split_kernel<V::KIND>, oa, ob, (int)a.K, pitch, ya);
+    }
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "split kernel: %s", cudaGetErrorString(e));
 
     const CUtensorMapDataType dt = V::KIND == kTcTf32     ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -234,7 +237,8 @@ VariantEntry tc_entry(const char *name) {
     v.desc.a_kmajor = 1;
     v.desc.threads = V::THREADS;
     v.desc.smem_bytes = V::SMEM_BYTES;
-    v.desc.trans_mask = V::FUSEB ? 5 : (V::FUSEA ? 3 : 15);  // fused B: transB = N only; fused A: transA = N only
+    // fused B: transB = N only; fused A: transA = N only; both: N N only
+    v.desc.trans_mask = V::FUSE == 3 ? 1 : (V::FUSEB ? 5 : (V::FUSEA ? 3 : 15));
     v.desc.kind = V::KIND == kTcTf32 ? 1 : (V::KIND == kTcBf16x3 ? 2 : 3);
     v.desc.schedule = V::STREAMK ? PT_SCHED_STREAMK : (V::SPLITK > 1 ? PT_SCHED_TILE : PT_SCHED_PERSISTENT);
     std::strncpy(v.desc.name, name, sizeof(v.desc.name) - 1);
@@ -311,6 +315,13 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcBf16x3, 128, 3, 2, 64, 0, 1>>("tcbf16x3_m128n128_p3_sw64_fb_sk2"),
         tc_entry<Tc<kTcBf16x3, 128, 3, 4, 64, 0, 1>>("tcbf16x3_m128n128_p3_sw64_fb_sk4"),
         tc_entry<Tc<kTcBf16x3, 128, 3, 1, 64, 1, 1>>("tcbf16x3_m128n128_p3_sw64_fb_stk"),
+        // Both operands split inside the GEMM kernel: one launch per call,
+        // for small problems whose time is mostly the fixed cost per launch.
+        tc_entry<Tc<kTcBf16x3, 64, 3, 1, 64, 0, 3>>("tcbf16x3_m128n64_p3_sw64_fab"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 2, 64, 0, 3>>("tcbf16x3_m128n64_p3_sw64_fab_sk2"),
+        tc_entry<Tc<kTcBf16x3, 64, 3, 4, 64, 0, 3>>("tcbf16x3_m128n64_p3_sw64_fab_sk4"),
+        tc_entry<Tc<kTcBf16x3, 128, 2, 1, 64, 0, 3>>("tcbf16x3_m128n128_p2_sw64_fab"),
+        tc_entry<Tc<kTcBf16x3, 128, 2, 4, 64, 0, 3>>("tcbf16x3_m128n128_p2_sw64_fab_sk4"),
         // 32-column tiles: twice the CTAs of 64-column ones on skinny,
         // long-K shapes (5-10 % faster there; more A re-reads elsewhere).
         tc_entry<Tc<kTcBf16x3, 32, 3, 4>>("tcbf16x3_m128n32_p3_sk4"),

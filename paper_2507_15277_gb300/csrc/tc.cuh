@@ -76,9 +76,11 @@ struct Tc {
     // itself and four converter warps write its three planes into the stage,
     // so that operand never passes through the split kernel.  FUSE = 1: B
     // (stored K x N, N contiguous; pays for small M); FUSE = 2: A (stored
-    // M x K, K contiguous; pays for small N).
+    // M x K, K contiguous; pays for small N); FUSE = 3: both, so a call is a
+    // single launch (pays for small problems, whose time is mostly the fixed
+    // cost of each launch).
     static constexpr int FUSE = FUSE_;
-    static constexpr bool FUSEB = FUSE == 1, FUSEA = FUSE == 2;
+    static constexpr bool FUSEB = FUSE == 1 || FUSE == 3, FUSEA = FUSE == 2 || FUSE == 3;
     static_assert(FUSE == 0 || KIND_ == kTcBf16x3, "fused split is BF16x3 only");
     // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
     // A narrower row makes the stage smaller, so more stages fit and the
@@ -107,12 +109,14 @@ struct Tc {
     static constexpr int CHUNK_KT = CHUNK_K / BK;
     static constexpr int A_PLANE_BYTES = BM * SWZ;
     static constexpr int B_PLANE_BYTES = BN * SWZ;
-    // FP32 tile of the fused operand: B as [BK][BN], A as [BM][BK].
-    static constexpr int F32_BYTES = FUSEB ? BK * BN * 4 : (FUSEA ? BM * BK * 4 : 0);
+    // FP32 tiles of the fused operands after the planes: A as [BM][BK] (at
+    // F32A_OFFSET), then B as [BK][BN] (at F32B_OFFSET).
+    static constexpr int F32A_BYTES = FUSEA ? BM * BK * 4 : 0, F32B_BYTES = FUSEB ? BK * BN * 4 : 0;
+    static constexpr int F32_BYTES = F32A_BYTES + F32B_BYTES;
+    static constexpr int F32A_OFFSET = P * (A_PLANE_BYTES + B_PLANE_BYTES), F32B_OFFSET = F32A_OFFSET + F32A_BYTES;
     static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES) + F32_BYTES;
-    static constexpr int LOAD_BYTES = FUSEB   ? P * A_PLANE_BYTES + F32_BYTES
-                                      : FUSEA ? P * B_PLANE_BYTES + F32_BYTES
-                                              : STAGE_BYTES;  // bytes the TMA loads deliver per stage
+    // bytes the TMA loads deliver per stage
+    static constexpr int LOAD_BYTES = (FUSEA ? F32A_BYTES : P * A_PLANE_BYTES) + (FUSEB ? F32B_BYTES : P * B_PLANE_BYTES);
     static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
     // Barriers (full, empty per stage; converted per stage when FUSEB; two
     // accumulator-full, two accumulator-empty, MMA-done) and the TMEM address
@@ -281,7 +285,7 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
 }
 
 // Fused split: converting thread ct (0 <= ct < V::CONV_THREADS) writes its
-// share of the stage's three BF16 planes of the fused operand from the FP32
+// share of the stage's three BF16 planes of each fused operand from the FP32
 // tile the producer loaded, K-major in the swizzled layout a TMA load would
 // produce (16-byte chunk c of plane row r at chunk c ^ ((r * SWZ / 128) &
 // (SWZ / 16 - 1))).  x = b0 + b1 + b2 with b0 = RN_bf16(x), b1 = RN_bf16(x - b0),
@@ -289,9 +293,9 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
 template <class V>
 __device__ __forceinline__ void tc_convert_stage(unsigned char *stp, int ct) {
     constexpr int BK = V::BK, BN = V::BN, P = V::P, KC = BK / 8, NCT = V::CONV_THREADS;
-    const float *bf = reinterpret_cast<const float *>(stp + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES));
-    unsigned char *bp = stp + (V::FUSEB ? P * V::A_PLANE_BYTES : 0);
     if constexpr (V::FUSEB) {
+        const float *bf = reinterpret_cast<const float *>(stp + V::F32B_OFFSET);
+        unsigned char *bp = stp + P * V::A_PLANE_BYTES;
         // B: lanes take consecutive n of one k chunk (the FP32 tile is
         // [k][n]) and each writes one 16-byte chunk of every plane.
 #pragma unroll 2
@@ -319,10 +323,13 @@ __device__ __forceinline__ void tc_convert_stage(unsigned char *stp, int ct) {
                 *reinterpret_cast<uint4 *>(bp + pl * V::B_PLANE_BYTES + off) =
                     make_uint4(b[pl][0], b[pl][1], b[pl][2], b[pl][3]);
         }
-    } else {
+    }
+    if constexpr (V::FUSEA) {
         // A: consecutive lanes read consecutive 16-byte pieces of the [m][k]
         // tile (no bank conflicts); a piece is four k values, half of one
         // 16-byte plane chunk.
+        const float *bf = reinterpret_cast<const float *>(stp + V::F32A_OFFSET);
+        unsigned char *bp = stp;
         constexpr int HC = 2 * KC;  // pieces per row
 #pragma unroll 2
         for (int it = ct; it < V::BM * HC; it += NCT) {
@@ -477,8 +484,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::LOAD_BYTES);
                     if constexpr (V::FUSEA) {
                         // FP32 tile of A: BM rows, BK columns of k (2-D map over A itself).
-                        tma_load_2d(st + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES), &mapA, full0 + 8 * s,
-                                    (kt0 + kt) * BK, m0);
+                        tma_load_2d(st + V::F32A_OFFSET, &mapA, full0 + 8 * s, (kt0 + kt) * BK, m0);
                     } else {
 #pragma unroll
                         for (int p = 0; p < P; ++p)
@@ -486,8 +492,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     }
                     if constexpr (V::FUSEB) {
                         // FP32 tile of B: BK rows of k, BN columns of n (2-D map over B itself).
-                        tma_load_2d(st + P * (V::A_PLANE_BYTES + V::B_PLANE_BYTES), &mapB, full0 + 8 * s, n0,
-                                    (kt0 + kt) * BK);
+                        tma_load_2d(st + V::F32B_OFFSET, &mapB, full0 + 8 * s, n0, (kt0 + kt) * BK);
                     } else {
 #pragma unroll
                         for (int p = 0; p < P; ++p)

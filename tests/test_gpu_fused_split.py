@@ -131,3 +131,53 @@ def test_fused_a_declines_unreadable_a():
     with pytest.raises(pt.PtError) as e:
         pt.sgemm(At, B, transA="T", variant=vid)
     assert e.value.code == pt._lib.PT_EUNSUPPORTED
+
+
+PAIRS_AB = [("tcbf16x3_m128n64_p3_sw64_fab", "tcbf16x3_m128n64_p4_sw64"),
+            ("tcbf16x3_m128n64_p3_sw64_fab_sk2", "tcbf16x3_m128n64_p4_sw64_sk2"),
+            ("tcbf16x3_m128n64_p3_sw64_fab_sk4", "tcbf16x3_m128n64_p4_sw64_sk4"),
+            ("tcbf16x3_m128n128_p2_sw64_fab", "tcbf16x3_m128n128_p4_sw64"),
+            ("tcbf16x3_m128n128_p2_sw64_fab_sk4", "tcbf16x3_m128n128_p4_sw64_sk4")]
+SHAPES_AB = [(128, 128, 128), (300, 200, 520), (640, 320, 2176), (1024, 1024, 512), (128, 128, 4096)]
+
+
+@pytest.mark.parametrize("fused,plain", PAIRS_AB)
+@pytest.mark.parametrize("shape", SHAPES_AB)
+def test_fused_both_matches_split_kernel_and_oracle(fused, plain, shape):
+    # Both operands split inside the GEMM kernel (one launch): the same planes
+    # and the same chunk order (and split-K slices) as the twin that splits
+    # both in the split kernel, so the same bits.
+    M, N, K = shape
+    A = matrix("uniform", 71, M, K)
+    B = matrix("uniform", 72, K, N)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    Cf = pt.sgemm(Ad, Bd, variant=pt.variant_by_name(fused))
+    Cp = pt.sgemm(Ad, Bd, variant=pt.variant_by_name(plain))
+    torch.cuda.synchronize()
+    cf = Cf.cpu().numpy()
+    assert np.array_equal(cf, Cp.cpu().numpy())
+    rows = np.arange(0, M, max(1, M // 64))
+    ref = og.gemm(A, B, rows=rows)
+    assert normalised_error(cf[rows], ref, K, np.abs(A).max(), np.abs(B).max()) <= TOL_FP32
+    assert pt.device_status() == 0
+
+
+@pytest.mark.parametrize("fused", [p[0] for p in PAIRS_AB])
+def test_fused_both_integers_alpha_beta_and_declines(fused):
+    M, N, K = 200, 136, 1032
+    A = matrix("ints", 81, M, K)
+    B = matrix("ints", 82, K, N)
+    C0 = matrix("ints", 83, M, N)
+    ref = og.gemm(A, B, alpha=2.0, beta=-1.0, C=C0)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    C = torch.from_numpy(C0.copy()).to(DEV)
+    vid = pt.variant_by_name(fused)
+    pt.sgemm(Ad, Bd, C, alpha=2.0, beta=-1.0, variant=vid)
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
+    for ta, tb in (("T", "N"), ("N", "T")):     # only A as M x K and B as K x N are read in the kernel
+        At = Ad if ta == "N" else Ad.t().contiguous()
+        Bt = Bd if tb == "N" else Bd.t().contiguous()
+        with pytest.raises(pt.PtError) as e:
+            pt.sgemm(At, Bt, transA=ta, transB=tb, variant=vid)
+        assert e.value.code == pt._lib.PT_EUNSUPPORTED

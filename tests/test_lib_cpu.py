@@ -51,7 +51,8 @@ def test_registry_rules():
             assert d["kind"] in (1, 2, 3) and d["bm"] == 128 and d["bn"] in (32, 64, 128)
             assert d["name"].startswith({1: "tc3xtf32_", 2: "tcbf16x3_", 3: "tc3xf16_"}[d["kind"]])
             # fused versions read B (or A) themselves: transB (transA) = 'N' only; the others take any layout
-            assert d["loader"] == 1 and d["trans_mask"] == (5 if "_fb" in d["name"] else 3 if "_fa" in d["name"] else 15)
+            assert d["loader"] == 1 and d["trans_mask"] == (1 if "_fab" in d["name"] else 5 if "_fb" in d["name"]
+                                                            else 3 if "_fa" in d["name"] else 15)
             # epilogue + producer + MMA warps (+ four converter warps when B is split in the kernel)
             fused = "_fb" in d["name"] or "_fa" in d["name"]
             conv = (2 if d["bn"] >= 128 else 4) if fused else 0  # converter warps
