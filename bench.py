@@ -1248,7 +1248,7 @@ def main():
                    "train_split": "parity (i_m+i_n+i_k even) 32/32",
                    "l2": "inputs 1.6 GB (> 129 MB L2) read once per step; no flush needed",
                    "timed": "CUDA graph of the 64 pt_sgemm launches, replayed per step",
-                   "compute": "FP32 in/out; per shape the selector picks FP32-FMA SIMT or BF16x3/3xTF32 tensor-core "
+                   "compute": "FP32 in/out; per shape the selector picks FP32-FMA SIMT or 3xF16/BF16x3/3xTF32 tensor-core "
                               "splits with FP32 accumulation",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "clocks": clk,
