@@ -99,7 +99,9 @@ int pt_sgemm_reference(char transA, char transB, int64_t M, int64_t N, int64_t K
 
 typedef struct pt_variant_desc {
     int id;
-    int bm, bn, bk;    /* CTA tile M x N and K-step                          */
+    int bm, bn, bk;    /* CTA tile M x N and K-step (two-CTA tensor-core
+                          versions, names ending in _2sm: bm = 256 is the
+                          tile of the CTA pair, 128 rows per CTA)       */
     int wm, wn;        /* warp tile                                          */
     int tm, tn;        /* per-thread register tile                           */
     int kl;            /* k-groups of lanes inside a warp, shuffle-reduced   */

@@ -80,9 +80,44 @@ int make_map_3d(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int 
 
 inline int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 
+// Pair versions: how many CTA pairs of this kernel can be resident at once
+// (clusters of two need two free SMs of one GPC), so the persistent grid is
+// a single wave.  Cached per device.
+template <class V>
+int max_pairs(int dev, int sms) {
+    static std::atomic<int> cap[64];
+    int c = dev < 64 ? cap[dev].load(std::memory_order_relaxed) : 0;
+    if (c > 0) return c;
+    c = std::max(1, sms / 2);
+    if (cudaFuncSetAttribute(tc_sgemm_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, V::SMEM_BYTES) ==
+        cudaSuccess) {
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3((unsigned)(2 * c), 1, 1);
+        cfg.blockDim = dim3(V::THREADS, 1, 1);
+        cfg.dynamicSmemBytes = V::SMEM_BYTES;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, tc_sgemm_kernel<V>, &cfg) == cudaSuccess && n > 0)
+            c = std::min(c, n);
+        else
+            (void)cudaGetLastError();
+    } else {
+        (void)cudaGetLastError();
+    }
+    if (dev < 64) cap[dev].store(c, std::memory_order_relaxed);
+    return c;
+}
+
 template <class V>
 int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
-    const int64_t tiles = (((int64_t)a.M + V::BM - 1) / V::BM) * (((int64_t)a.N + V::BN - 1) / V::BN);
+    const int64_t tiles = (((int64_t)a.M + V::TILE_M - 1) / V::TILE_M) * (((int64_t)a.N + V::BN - 1) / V::BN);
     if (tiles > 0x7fffffff || ((int64_t)a.M + 31) / 32 + ((int64_t)a.N + 31) / 32 > 65535)
         return set_error(PT_EUNSUPPORTED, 3, "shape too large for this variant's grid");
     // Row pitch: a multiple of 8 elements (16-byte aligned rows, whole
@@ -109,6 +144,9 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
         if (V::STREAMK) {
             const int64_t nch = (((int64_t)a.K + V::BK - 1) / V::BK + V::CHUNK_KT - 1) / V::CHUNK_KT;
             grid = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(sms, kSkMaxGrid), tiles * nch));
+        } else if (V::PAIR) {
+            // Two CTAs per tile, at most as many pairs as fit on the device at once.
+            grid = 2 * std::min<int64_t>(tiles, max_pairs<V>(dev, sms));
         } else if (grid > sms) {
             grid = sms;
         }
@@ -119,7 +157,7 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int64_t header = align256((int64_t)kSkHeaderBytes);
     const int64_t partials = V::STREAMK ? align256(grid * V::BM * V::BN * 4) : 0;
     const int64_t nchk = ((int64_t)a.K + V::CHUNK_K - 1) / V::CHUNK_K;
-    const int64_t ld_sa = ((int64_t)a.M + 127) / 128 * 128, ld_sb = ((int64_t)a.N + 127) / 128 * 4;
+    const int64_t ld_sa = ((int64_t)a.M + V::TILE_M - 1) / V::TILE_M * V::TILE_M, ld_sb = ((int64_t)a.N + 127) / 128 * 4;
     const int64_t sa_bytes = V::SCALED ? align256(nchk * ld_sa * 4) : 0;
     const int64_t sb_bytes = V::SCALED ? align256(nchk * ld_sb * 4) : 0;
     const size_t need =
@@ -177,7 +215,7 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     if (V::FUSEB)
         rc = make_map_2d(&mB, a.B, a.N, a.K, a.ldb, V::BN, V::BK, CU_TENSOR_MAP_SWIZZLE_NONE);
     else
-        rc = make_map_3d(&mB, wB, dt, V::ELEM, a.K, a.N, V::P, pitch * V::ELEM, b_plane, V::BK, V::BN, V::SWZ);
+        rc = make_map_3d(&mB, wB, dt, V::ELEM, a.K, a.N, V::P, pitch * V::ELEM, b_plane, V::BK, V::B_ROWS, V::SWZ);
     if (rc != PT_OK) return rc;
 
     TcArgs t;
@@ -205,9 +243,9 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     cfg.stream = st;
     cudaLaunchAttribute attr[2];
     unsigned nattr = 0;
-    if (V::SPLITK > 1) {
+    if (V::SPLITK > 1 || V::PAIR) {
         attr[nattr].id = cudaLaunchAttributeClusterDimension;
-        attr[nattr].val.clusterDim.x = 1;
+        attr[nattr].val.clusterDim.x = V::PAIR ? 2 : 1;
         attr[nattr].val.clusterDim.y = 1;
         attr[nattr].val.clusterDim.z = V::SPLITK;
         ++nattr;
@@ -226,7 +264,7 @@ template <class V>
 VariantEntry tc_entry(const char *name) {
     VariantEntry v;
     std::memset(&v.desc, 0, sizeof(v.desc));
-    v.desc.bm = V::BM;
+    v.desc.bm = V::TILE_M;  // pair versions: the 256-row tile of a CTA pair
     v.desc.bn = V::BN;
     v.desc.bk = V::BK;
     v.desc.kl = 1;
@@ -350,6 +388,9 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcF16s, 64, 4, 8>>("tc3xf16_m128n64_p4_sk8"),
         tc_entry<Tc<kTcF16s, 32, 5, 4>>("tc3xf16_m128n32_p5_sk4"),
         tc_entry<Tc<kTcF16s, 32, 5, 8>>("tc3xf16_m128n32_p5_sk8"),
+        // CTA pairs (cta_group::2): 256 x 128 tiles, four 48 KB stages.
+        tc_entry<Tc<kTcF16s, 128, 4, 1, 128, 0, 0, 1>>("tc3xf16_m256n128_p4_2sm"),
+        tc_entry<Tc<kTcTf32, 128, 4, 1, 128, 0, 0, 1>>("tc3xtf32_m256n128_p4_2sm"),
     };
 }
 

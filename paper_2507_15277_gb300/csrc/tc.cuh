@@ -63,7 +63,8 @@
 
 namespace pt {
 
-template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128, int STREAMK_ = 0, int FUSE_ = 0>
+template <int KIND_, int BN_, int STAGES_, int SPLITK_ = 1, int SWZ_ = 128, int STREAMK_ = 0, int FUSE_ = 0,
+          int PAIR_ = 0>
 struct Tc {
     static constexpr int KIND = KIND_, BM = 128, BN = BN_, STAGES = STAGES_, SPLITK = SPLITK_;
     // Stream-K (SPLITK == 1 only): the grid's CTAs split tiles x chunks into
@@ -82,6 +83,17 @@ struct Tc {
     static constexpr int FUSE = FUSE_;
     static constexpr bool FUSEB = FUSE == 1 || FUSE == 3, FUSEA = FUSE == 2 || FUSE == 3;
     static_assert(FUSE == 0 || KIND_ == kTcBf16x3, "fused split is BF16x3 only");
+    // Two-CTA pair (cta_group::2): a cluster (2,1,1) computes 256 x BN tiles
+    // with M = 256 MMAs that its even CTA issues.  Each CTA loads its 128 rows
+    // of A and half of the tile's BN rows of op(B)^T, so a stage holds 3/4 of
+    // the bytes of a one-CTA stage for the same MMA work per SM and one more
+    // stage fits.  The products are not paired along N (three N = BN MMAs per
+    // k step): the two halves of B sit in different CTAs.
+    static constexpr bool PAIR = PAIR_ != 0;
+    static_assert(!PAIR || (SPLITK_ == 1 && STREAMK_ == 0 && FUSE_ == 0 && BN_ == 128 && KIND_ != kTcBf16x3),
+                  "pair versions: persistent, unfused, 128 columns, three products");
+    static constexpr int TILE_M = PAIR ? 256 : 128;  // rows of a scheduled tile
+    static constexpr int B_ROWS = PAIR ? BN_ / 2 : BN_;  // rows of op(B)^T a CTA loads per tile
     // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
     // A narrower row makes the stage smaller, so more stages fit and the
     // producer refills a smaller part of the pipeline at a time.
@@ -98,7 +110,7 @@ struct Tc {
     static constexpr int KSTEP = 32 / ELEM;               // K of one MMA instruction (32 bytes)
     static constexpr int NPROD = KIND == kTcBf16x3 ? 6 : 3;
     // MMA instructions per k step after pairing along N (see tc_op).
-    static constexpr int NOPS = KIND == kTcBf16x3 ? 4 : 2;
+    static constexpr int NOPS = PAIR ? 3 : (KIND == kTcBf16x3 ? 4 : 2);
     // Promotion: the tensor-core accumulator is restarted every CHUNK_KT
     // k-tiles (CHUNK_K values of k) and added into FP32 registers with IEEE
     // round-to-nearest, so the accumulation error grows with CHUNK_K, not K.
@@ -108,7 +120,7 @@ struct Tc {
     static constexpr int CHUNK_K = SCALED ? 256 : 128;
     static constexpr int CHUNK_KT = CHUNK_K / BK;
     static constexpr int A_PLANE_BYTES = BM * SWZ;
-    static constexpr int B_PLANE_BYTES = BN * SWZ;
+    static constexpr int B_PLANE_BYTES = B_ROWS * SWZ;
     // FP32 tiles of the fused operands after the planes: A as [BM][BK] (at
     // F32A_OFFSET), then B as [BK][BN] (at F32B_OFFSET).
     static constexpr int F32A_BYTES = FUSEA ? BM * BK * 4 : 0, F32B_BYTES = FUSEB ? BK * BN * 4 : 0;
@@ -116,7 +128,9 @@ struct Tc {
     static constexpr int F32A_OFFSET = P * (A_PLANE_BYTES + B_PLANE_BYTES), F32B_OFFSET = F32A_OFFSET + F32A_BYTES;
     static constexpr int STAGE_BYTES = P * (A_PLANE_BYTES + B_PLANE_BYTES) + F32_BYTES;
     // bytes the TMA loads deliver per stage
-    static constexpr int LOAD_BYTES = (FUSEA ? F32A_BYTES : P * A_PLANE_BYTES) + (FUSEB ? F32B_BYTES : P * B_PLANE_BYTES);
+    // (pair versions: both CTAs' loads complete on the even CTA's barrier)
+    static constexpr int LOAD_BYTES =
+        (PAIR ? 2 : 1) * ((FUSEA ? F32A_BYTES : P * A_PLANE_BYTES) + (FUSEB ? F32B_BYTES : P * B_PLANE_BYTES));
     static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
     // Barriers (full, empty per stage; converted per stage when FUSEB; two
     // accumulator-full, two accumulator-empty, MMA-done) and the TMEM address
@@ -159,7 +173,7 @@ struct Tc {
     // N >> 3 at bit 17, M >> 4 at bit 24.
     static constexpr uint32_t FMT = KIND == kTcTf32 ? 2u : (KIND == kTcBf16x3 ? 1u : 0u);
     static constexpr uint32_t IDESC =
-        (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+        (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TILE_M >> 4) << 24);
     static constexpr uint32_t IDESC_W =
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     static_assert(BN == 32 || BN == 64 || BN == 128, "N of the MMA (2*BN <= 256, a multiple of 16)");
@@ -168,7 +182,7 @@ struct Tc {
     static_assert(BM % SPLITK == 0, "split-K reduction slices rows");
     // Consecutive CTAs walk GROUP_M tile rows down before moving right, so a
     // wave's A and B panels stay in L2.
-    static constexpr int GROUP_M = 8;
+    static constexpr int GROUP_M = PAIR ? 4 : 8;
     static_assert(TMEM_COLS <= 512, "tensor memory columns");
     static_assert(EPI_WARPS <= 8, "stream-K flag slots per CTA");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
@@ -368,8 +382,16 @@ __device__ __forceinline__ void tc_tile_coords(int t, int tiles_m, int tiles_n, 
     const int first_m = (t / per_group) * V::GROUP_M;
     const int gsize = tiles_m - first_m < V::GROUP_M ? tiles_m - first_m : V::GROUP_M;
     const int r = t % per_group;
-    m0 = (first_m + r % gsize) * V::BM;
+    m0 = (first_m + r % gsize) * V::TILE_M;
     n0 = (r / gsize) * V::BN;
+}
+
+// This CTA's rows of tile t: pair versions split the 256 rows between the
+// two CTAs of the cluster by rank.
+template <class V>
+__device__ __forceinline__ void tc_cta_coords(int t, int tiles_m, int tiles_n, uint32_t rank, int &m0, int &n0) {
+    tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
+    if constexpr (V::PAIR) m0 += (int)rank * V::BM;
 }
 
 // SPLITK == 1: persistent; CTA b computes tiles b, b + gridDim.x, ...  The
@@ -382,7 +404,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     const __grid_constant__ CUtensorMap mapB) {
     constexpr int STAGES = V::STAGES, BK = V::BK, BN = V::BN, P = V::P, CKT = V::CHUNK_KT, COLS = V::COLS;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ int s_fail, s_issued, s_consumed;
+    __shared__ int s_fail, s_issued, s_consumed, s_peer_issued;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
     const uint32_t full0 = sbase + V::BAR_OFFSET;  // STAGES: TMA landed
@@ -396,9 +418,11 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         reinterpret_cast<const volatile uint32_t *>(smem_raw + (tslot - raw));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tiles_m = (args.M + V::BM - 1) / V::BM, tiles_n = (args.N + BN - 1) / BN;
+    const int tiles_m = (args.M + V::TILE_M - 1) / V::TILE_M, tiles_n = (args.N + BN - 1) / BN;
     const int tiles = tiles_m * tiles_n;
-    const int t_first = (int)blockIdx.x;
+    // Pair versions: the cluster (2,1,1) is the scheduling unit; rank 0 issues the MMAs.
+    const uint32_t rank = V::PAIR ? cluster_ctarank() : 0u;
+    const int t_first = V::PAIR ? (int)blockIdx.x / 2 : (int)blockIdx.x;
     // K range (k-tiles) of this CTA; the same for every tile.
     const int kt_total = (args.K + BK - 1) / BK;
     int kt0 = 0, nkt = kt_total;
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     TcWork work;
     work.nch = nchunks;
     work.t_first = t_first;
-    work.t_step = V::SPLITK > 1 ? tiles : (int)gridDim.x;  // split-K: exactly one tile
+    work.t_step = V::SPLITK > 1 ? tiles : (V::PAIR ? (int)gridDim.x / 2 : (int)gridDim.x);  // split-K: one tile
     work.tiles = tiles;
     work.streamk = V::STREAMK != 0;
     // Stream-K: whole tiles for all but the last full wave, then the rest
@@ -439,20 +463,27 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf0 + 8 * b, 1);
-            mbar_init(acce0 + 8 * b, V::EPI_WARPS);
+            mbar_init(acce0 + 8 * b, (V::PAIR ? 2 : 1) * V::EPI_WARPS);  // pair: both CTAs' drains
         }
         mbar_init(doneb, 1);
         fence_mbarrier_init();
         s_fail = 0;
         s_issued = 0;
         s_consumed = 0;
+        s_peer_issued = 0;
     }
     if (warp == 0) {
-        tmem_alloc(tslot, V::TMEM_COLS);
-        tmem_relinquish();
+        if constexpr (V::PAIR) {
+            tmem_alloc_pair(tslot, V::TMEM_COLS);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(tslot, V::TMEM_COLS);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (V::PAIR) cluster_sync();  // the peer's barriers are initialised before any remote arrival
     tc_fence_after();
     const uint32_t tmem = *tslot_ptr;
     // The prologue above touches no global memory; from here on the previous
@@ -471,7 +502,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 int t, c0, c1;
                 work.seg(i, t, c0, c1);
                 int m0, n0;
-                tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
+                tc_cta_coords<V>(t, tiles_m, tiles_n, rank, m0, n0);
+                const int nb = n0 + (int)rank * V::B_ROWS;  // pair versions: this CTA's half of the B rows
                 const int kt_end = c1 * CKT < nkt ? c1 * CKT : nkt;
                 for (int kt = c0 * CKT; kt < kt_end; ++kt, ++g) {
                     const int s = g % STAGES, u = g / STAGES;
@@ -481,7 +513,22 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         break;
                     }
                     const uint32_t st = sbase + s * V::STAGE_BYTES;
-                    mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::LOAD_BYTES);
+                    if constexpr (V::PAIR) {
+                        // Both CTAs' copies complete on the even CTA's barrier, which
+                        // expects the bytes of both.
+                        const uint32_t lead_full = mapa_shared(full0 + 8 * s, 0u);
+                        if (rank == 0) mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::LOAD_BYTES);
+#pragma unroll
+                        for (int p = 0; p < P; ++p)
+                            tma_load_3d_pair(st + p * V::A_PLANE_BYTES, &mapA, lead_full, (kt0 + kt) * BK, m0, p);
+#pragma unroll
+                        for (int p = 0; p < P; ++p)
+                            tma_load_3d_pair(st + P * V::A_PLANE_BYTES + p * V::B_PLANE_BYTES, &mapB, lead_full,
+                                             (kt0 + kt) * BK, nb, p);
+                        continue;
+                    } else {
+                        mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)V::LOAD_BYTES);
+                    }
                     if constexpr (V::FUSEA) {
                         // FP32 tile of A: BM rows, BK columns of k (2-D map over A itself).
                         tma_load_2d(st + V::F32A_OFFSET, &mapA, full0 + 8 * s, (kt0 + kt) * BK, m0);
@@ -504,7 +551,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             s_issued = g;
         }
     } else if (warp == V::MMA_WARP) {
-        if (lane == 0) {
+        if (lane == 0 && rank == 0) {  // pair versions: the even CTA issues for both
             int g = 0, c = 0, b = 0;  // k-tiles consumed, chunks started (all segments)
             bool ok = true;
             for (int i = 0; ok && i < nseg; ++i) {
@@ -517,7 +564,9 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     if (first) {
                         b = c & 1;
                         // Buffer b was last used by chunk c - 2; wait until it is drained.
-                        if (c >= 2 && !mbar_wait_bounded(acce0 + 8 * b, (uint32_t)(((c >> 1) - 1) & 1), kWaitLimitNs)) {
+                        const uint32_t par = (uint32_t)(((c >> 1) - 1) & 1);
+                        if (c >= 2 && !(V::PAIR ? mbar_wait_cluster_bounded(acce0 + 8 * b, par, kWaitLimitNs)
+                                                : mbar_wait_bounded(acce0 + 8 * b, par, kWaitLimitNs))) {
                             s_fail = 1;
                             ok = false;
                             break;
@@ -532,28 +581,54 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     tc_fence_after();
                     const uint32_t st = sbase + s * V::STAGE_BYTES;
                     const uint32_t dt = tmem + (uint32_t)(b * V::ACC_COLS);
+                    if constexpr (V::PAIR) {
+                        // A0 B0 into the left half; A0 B1 and A1 B0 into the right half.
 #pragma unroll
-                    for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
+                        for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
 #pragma unroll
-                        for (int q = 0; q < V::NOPS; ++q) {
-                            int pa, pb;
-                            bool wide;
-                            tc_op<V::KIND>(q, pa, pb, wide);
-                            const uint64_t ad = kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
-                            const uint64_t bd = kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
-                                                (uint64_t)(2 * kk);
-                            tc_mma<V::KIND>(wide ? dt : dt + (uint32_t)BN, ad, bd, wide ? V::IDESC_W : V::IDESC,
-                                            (first && kk == 0 && q == 0) ? 0u : 1u);
+                            for (int q = 0; q < 3; ++q) {
+                                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                                const uint64_t ad = kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                                const uint64_t bd =
+                                    kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
+                                    (uint64_t)(2 * kk);
+                                tc_mma_pair<V::KIND>(q == 0 ? dt : dt + (uint32_t)BN, ad, bd, V::IDESC,
+                                                     (first && kk == 0 && q < 2) ? 0u : 1u);
+                            }
                         }
-                    }
-                    tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
-                    if ((kt % CKT) == CKT - 1 || kt == kt_end - 1) {
-                        tc_commit(accf0 + 8 * b);  // chunk c complete
-                        ++c;
+                        tc_commit_pair(empty0 + 8 * s);
+                        if ((kt % CKT) == CKT - 1 || kt == kt_end - 1) {
+                            tc_commit_pair(accf0 + 8 * b);
+                            ++c;
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
+#pragma unroll
+                            for (int q = 0; q < V::NOPS; ++q) {
+                                int pa, pb;
+                                bool wide;
+                                tc_op<V::KIND>(q, pa, pb, wide);
+                                const uint64_t ad = kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                                const uint64_t bd =
+                                    kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
+                                    (uint64_t)(2 * kk);
+                                tc_mma<V::KIND>(wide ? dt : dt + (uint32_t)BN, ad, bd, wide ? V::IDESC_W : V::IDESC,
+                                                (first && kk == 0 && q == 0) ? 0u : 1u);
+                            }
+                        }
+                        tc_commit(empty0 + 8 * s);  // stage s may be refilled once these MMAs finish
+                        if ((kt % CKT) == CKT - 1 || kt == kt_end - 1) {
+                            tc_commit(accf0 + 8 * b);  // chunk c complete
+                            ++c;
+                        }
                     }
                 }
             }
-            tc_commit(doneb);  // every MMA issued so far (also after a failure)
+            if constexpr (V::PAIR)
+                tc_commit_pair(doneb);  // every MMA issued so far (also after a failure), in both CTAs
+            else
+                tc_commit(doneb);  // every MMA issued so far (also after a failure)
             s_consumed = g;
         }
     } else if (V::FUSE && warp >= V::CONV_WARP0) {
@@ -608,7 +683,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             for (int q = 0; q < NG; ++q) sb_next[q] = 1.f;
             if constexpr (V::SCALED) {
                 int sm0, sn0;
-                tc_tile_coords<V>(t, tiles_m, tiles_n, sm0, sn0);
+                tc_cta_coords<V>(t, tiles_m, tiles_n, rank, sm0, sn0);
                 srow = sm0 + sub * 32 + lane;
                 sgrp = (sn0 + grp * COLS) / 32;
                 if (c0 < c1) {
@@ -683,7 +758,13 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acce0 + 8 * b);
+                if (lane == 0) {
+                    // Pair versions: the even CTA's MMA warp waits for the drains of both CTAs.
+                    if constexpr (V::PAIR)
+                        mbar_arrive_cluster(mapa_shared(acce0 + 8 * b, 0u));
+                    else
+                        mbar_arrive(acce0 + 8 * b);
+                }
                 ++c;
             }
             if (V::STREAMK != 0 && epi_ok && c1 < nchunks) {
@@ -732,7 +813,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 // staging buffer (row = lane in, four rows of 32 columns per
                 // instruction out).
                 int m0, n0;
-                tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
+                tc_cta_coords<V>(t, tiles_m, tiles_n, rank, m0, n0);
                 float *stg = reinterpret_cast<float *>(smem_raw + (sbase - raw) + V::STG_OFFSET) +
                              warp * V::STG_WARP_FLOATS;
                 const int rr = lane >> 3, cc = (lane & 7) * 4;
@@ -771,7 +852,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 }
             } else if (V::SPLITK == 1 && epi_ok) {
                 int m0, n0;
-                tc_tile_coords<V>(t, tiles_m, tiles_n, m0, n0);
+                tc_cta_coords<V>(t, tiles_m, tiles_n, rank, m0, n0);
                 const int row = m0 + sub * 32 + lane;
                 const int cbase = n0 + grp * COLS;
                 if (row < args.M && cbase < args.N) {
@@ -871,21 +952,33 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         }
         cluster_sync();  // no CTA leaves while a peer may still read its tile
     }
+    if constexpr (V::PAIR) {
+        // The odd CTA's copies complete on the even CTA's barriers: the even CTA
+        // learns how many stages its peer issued.
+        if (rank == 1 && tid == 0) st_dsmem_u32(mapa_shared(smem_u32(&s_peer_issued), 0u), (uint32_t)s_issued);
+        cluster_sync();
+    }
     if (tid == 0) {
         // No MMA may still write tensor memory when it is freed, and no TMA
         // copy may still be landing when the CTA exits.
         if (!mbar_wait_bounded(doneb, 0u, kWaitLimitNs)) s_fail = 1;
         if (s_fail) {
             if (args.err) atomicOr(args.err, 1);
-            for (int q = s_consumed; q < s_issued; ++q)
-                (void)mbar_wait_bounded(full0 + 8 * (q % STAGES), (uint32_t)((q / STAGES) & 1), kWaitLimitNs);
+            const int issued = s_issued > s_peer_issued ? s_issued : s_peer_issued;
+            if (rank == 0)
+                for (int q = s_consumed; q < issued; ++q)
+                    (void)mbar_wait_bounded(full0 + 8 * (q % STAGES), (uint32_t)((q / STAGES) & 1), kWaitLimitNs);
         }
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (V::PAIR) cluster_sync();  // the odd CTA stays until the even one has waited
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, V::TMEM_COLS);
+        if constexpr (V::PAIR)
+            tmem_dealloc_pair(tmem, V::TMEM_COLS);
+        else
+            tmem_dealloc(tmem, V::TMEM_COLS);
     }
 }
 

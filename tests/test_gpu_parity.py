@@ -87,7 +87,7 @@ def _nvar():
 SMALL_SHAPES = [(131, 97, 75), (33, 260, 19)]
 
 
-@pytest.mark.parametrize("vid", range(448))
+@pytest.mark.parametrize("vid", range(456))
 def test_variant_bit_exact_small_integers(vid):
     if vid >= _nvar():
         pytest.skip("registry has fewer variants")
@@ -104,7 +104,7 @@ def test_variant_bit_exact_small_integers(vid):
     assert ran > 0
 
 
-@pytest.mark.parametrize("vid", range(448))
+@pytest.mark.parametrize("vid", range(456))
 def test_variant_uniform_within_bound(vid):
     if vid >= _nvar():
         pytest.skip("registry has fewer variants")

@@ -71,7 +71,7 @@ def _nvar():
     return pt.num_variants()
 
 
-@pytest.mark.parametrize("vid", range(448))
+@pytest.mark.parametrize("vid", range(456))
 def test_every_plane_bit_exact(vid):
     if vid >= _nvar():
         pytest.skip("registry has fewer variants")
