@@ -1028,8 +1028,11 @@ def main():
     # g+1 runs while group g computes and the results of group g-1 are copied
     # back (events order the stages of a group).  One copy per group and
     # direction keeps the per-copy overhead of the small shapes off the link.
-    # This is how a user of the API overlaps host data with compute; the host
-    # link, not the GEMMs, bounds it.
+    # Consecutive steps use two sets of device buffers in turn, so a step's
+    # copies need not wait for the previous step's GEMMs and copies of the
+    # same group: both copy directions stream without gaps.  This is how a
+    # user of the API overlaps host data with compute; the host link, not the
+    # GEMMs, bounds it.
     h2d = sum(a.numel() * 4 + b.numel() * 4 for a, b in zip(hostA, hostB))
     d2h = sum(c.numel() * 4 for c in hostC)
     n_groups = 16
@@ -1041,37 +1044,48 @@ def main():
             groups.append((lo, i + 1))
             lo, acc = i + 1, 0.0
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    ev_in = [torch.cuda.Event() for _ in groups]
-    ev_done = [torch.cuda.Event() for _ in groups]
-    ev_out = [torch.cuda.Event() for _ in groups]
+    # the second set of device buffers (the first is the resident one)
+    dev_in2 = torch.empty(o_in, dtype=torch.float32, device=dev)
+    dev_out2 = torch.empty(o_out, dtype=torch.float32, device=dev)
+    dev_in2.copy_(dev_in)
+    bufs = [(dev_in, dev_out, devA, devB, devC),
+            (dev_in2, dev_out2,
+             [dev_in2[in_off[i]:in_off[i] + M * K].view(M, K) for i, (M, N, K) in enumerate(shapes)],
+             [dev_in2[in_off[i] + M * K:in_off[i + 1]].view(K, N) for i, (M, N, K) in enumerate(shapes)],
+             [dev_out2[out_off[i]:out_off[i + 1]].view(M, N) for i, (M, N, K) in enumerate(shapes)])]
+    ev_in = [[torch.cuda.Event() for _ in groups] for _ in bufs]
+    ev_done = [[torch.cuda.Event() for _ in groups] for _ in bufs]
+    ev_out = [[torch.cuda.Event() for _ in groups] for _ in bufs]
 
-    def e2e_step():
+    def e2e_step(p):
+        d_in, d_out, dA, dB, dC = bufs[p]
         for g, (a, b) in enumerate(groups):
             with torch.cuda.stream(s_in):
-                s_in.wait_event(ev_done[g])  # the previous step's GEMMs of group g have read its inputs
-                dev_in[in_off[a]:in_off[b]].copy_(host_in[in_off[a]:in_off[b]], non_blocking=True)
-                ev_in[g].record(s_in)
-            stream.wait_event(ev_in[g])
-            stream.wait_event(ev_out[g])  # the previous step's copy of group g's results has finished
+                s_in.wait_event(ev_done[p][g])  # the GEMMs of group g that last used this buffer set are done
+                d_in[in_off[a]:in_off[b]].copy_(host_in[in_off[a]:in_off[b]], non_blocking=True)
+                ev_in[p][g].record(s_in)
+            stream.wait_event(ev_in[p][g])
+            stream.wait_event(ev_out[p][g])  # the last copy of group g's results out of this set has finished
             for i in range(a, b):
-                pt.sgemm(devA[i], devB[i], devC[i], stream=stream)
-            ev_done[g].record(stream)
+                pt.sgemm(dA[i], dB[i], dC[i], stream=stream)
+            ev_done[p][g].record(stream)
             with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_done[g])
-                host_out[out_off[a]:out_off[b]].copy_(dev_out[out_off[a]:out_off[b]], non_blocking=True)
-                ev_out[g].record(s_out)
+                s_out.wait_event(ev_done[p][g])
+                host_out[out_off[a]:out_off[b]].copy_(d_out[out_off[a]:out_off[b]], non_blocking=True)
+                ev_out[p][g].record(s_out)
 
-    for g in range(len(groups)):
-        ev_done[g].record(stream)
-        ev_out[g].record(s_out)
-    for _ in range(2):
-        e2e_step()
+    for p in range(len(bufs)):
+        for g in range(len(groups)):
+            ev_done[p][g].record(stream)
+            ev_out[p][g].record(s_out)
+    for w in range(2):
+        e2e_step(w % 2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e0.record(stream)
     s_in.wait_stream(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    for st in range(args.steps):
+        e2e_step(st % 2)
     stream.wait_stream(s_out)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -1089,24 +1103,24 @@ def main():
             ts = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
             ev_t[g] = ts
             with torch.cuda.stream(s_in):
-                s_in.wait_event(ev_done[g])
+                s_in.wait_event(ev_done[0][g])
                 ts[0].record(s_in)
                 dev_in[in_off[a]:in_off[b]].copy_(host_in[in_off[a]:in_off[b]], non_blocking=True)
                 ts[1].record(s_in)
-                ev_in[g].record(s_in)
-            stream.wait_event(ev_in[g])
-            stream.wait_event(ev_out[g])
+                ev_in[0][g].record(s_in)
+            stream.wait_event(ev_in[0][g])
+            stream.wait_event(ev_out[0][g])
             ts[2].record(stream)
             for i in range(a, b):
                 pt.sgemm(devA[i], devB[i], devC[i], stream=stream)
             ts[3].record(stream)
-            ev_done[g].record(stream)
+            ev_done[0][g].record(stream)
             with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_done[g])
+                s_out.wait_event(ev_done[0][g])
                 ts[4].record(s_out)
                 host_out[out_off[a]:out_off[b]].copy_(dev_out[out_off[a]:out_off[b]], non_blocking=True)
                 ts[5].record(s_out)
-                ev_out[g].record(s_out)
+                ev_out[0][g].record(s_out)
 
     torch.cuda.synchronize()
     t_first = torch.cuda.Event(enable_timing=True)
@@ -1261,7 +1275,8 @@ def main():
                 "h2d_gbs_alone": h2d / (h2d_ms * 1e-3) / 1e9, "d2h_gbs_alone": d2h / (d2h_ms * 1e-3) / 1e9,
                 "overlap": overlap,
                 "pipeline": "3 streams over %d groups of consecutive shapes (about equal bytes), one copy per group "
-                            "and direction: H2D of group g+1 | GEMMs of group g | D2H of group g-1" % len(groups)},
+                            "and direction: H2D of group g+1 | GEMMs of group g | D2H of group g-1; two device "
+                            "buffer sets, alternate steps" % len(groups)},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "eager_value": world * step_flops * args.steps / (eager_ms * 1e-3) / 1e12,

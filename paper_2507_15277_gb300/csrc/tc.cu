@@ -391,6 +391,10 @@ std::vector<VariantEntry> tc_variants() {
         // CTA pairs (cta_group::2): 256 x 128 tiles, four 48 KB stages.
         tc_entry<Tc<kTcF16s, 128, 4, 1, 128, 0, 0, 1>>("tc3xf16_m256n128_p4_2sm"),
         tc_entry<Tc<kTcTf32, 128, 4, 1, 128, 0, 0, 1>>("tc3xtf32_m256n128_p4_2sm"),
+        // 256-column tiles: three N = 256 MMAs per k step into one accumulator,
+        // four 48 KB stages of 64-byte rows.
+        tc_entry<Tc<kTcF16s, 256, 4, 1, 64>>("tc3xf16_m128n256_p4_sw64"),
+        tc_entry<Tc<kTcF16s, 256, 4, 1, 64, 1>>("tc3xf16_m128n256_p4_sw64_stk"),
     };
 }
 

@@ -93,6 +93,14 @@ struct Tc {
     static_assert(!PAIR || (SPLITK_ == 1 && STREAMK_ == 0 && FUSE_ == 0 && BN_ == 128 && KIND_ != kTcBf16x3),
                   "pair versions: persistent, unfused, 128 columns, three products");
     static constexpr int TILE_M = PAIR ? 256 : 128;  // rows of a scheduled tile
+    // 256-column tiles (three-product kinds, one CTA): every product is one
+    // N = 256 MMA into a single accumulator of 256 columns (no left / right
+    // halves), so a k step is three MMAs for twice the output of a 128-column
+    // tile's two (N = 256 + N = 128), and the two buffers still fit tensor
+    // memory.
+    static constexpr bool MERGED = BN_ == 256;
+    static_assert(!MERGED || (KIND_ != kTcBf16x3 && FUSE_ == 0 && !PAIR && SPLITK_ == 1),
+                  "256-column tiles: three-product kinds, unfused, one CTA, no split-K");
     static constexpr int B_ROWS = PAIR ? BN_ / 2 : BN_;  // rows of op(B)^T a CTA loads per tile
     // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
     // A narrower row makes the stage smaller, so more stages fit and the
@@ -110,7 +118,7 @@ struct Tc {
     static constexpr int KSTEP = 32 / ELEM;               // K of one MMA instruction (32 bytes)
     static constexpr int NPROD = KIND == kTcBf16x3 ? 6 : 3;
     // MMA instructions per k step after pairing along N (see tc_op).
-    static constexpr int NOPS = PAIR ? 3 : (KIND == kTcBf16x3 ? 4 : 2);
+    static constexpr int NOPS = (PAIR || MERGED) ? 3 : (KIND == kTcBf16x3 ? 4 : 2);
     // Promotion: the tensor-core accumulator is restarted every CHUNK_KT
     // k-tiles (CHUNK_K values of k) and added into FP32 registers with IEEE
     // round-to-nearest, so the accumulation error grows with CHUNK_K, not K.
@@ -138,7 +146,7 @@ struct Tc {
     static constexpr int BAR_BYTES = 8 * ((FUSE ? 3 : 2) * STAGES + 6);
 
     // Accumulator buffer: 2*BN columns (left half, right half); two buffers.
-    static constexpr int ACC_COLS = 2 * BN;
+    static constexpr int ACC_COLS = MERGED ? BN : 2 * BN;
     static constexpr int TMEM_COLS = 2 * ACC_COLS;
     // Epilogue warps: 4 per 128 columns (a warp reads its 32 TMEM lanes), each
     // thread owns one row and COLS columns; then one producer and one MMA warp.
@@ -176,7 +184,7 @@ struct Tc {
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TILE_M >> 4) << 24);
     static constexpr uint32_t IDESC_W =
         (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)((2 * BN) >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-    static_assert(BN == 32 || BN == 64 || BN == 128, "N of the MMA (2*BN <= 256, a multiple of 16)");
+    static_assert(BN == 32 || BN == 64 || BN == 128 || MERGED, "N of the MMA (2*BN <= 256, a multiple of 16)");
     static_assert(FUSE == 0 || BN >= 64, "fused versions use 64- or 128-column tiles");
     static_assert(SPLITK == 1 || BM * RED_LD * 4 <= BAR_OFFSET, "split-K partial tile fits the pipeline memory");
     static_assert(BM % SPLITK == 0, "split-K reduction slices rows");
@@ -601,6 +609,25 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                             tc_commit_pair(accf0 + 8 * b);
                             ++c;
                         }
+                    } else if constexpr (V::MERGED) {
+                        // A0 B0, A0 B1, A1 B0, each N = 256, into the same columns.
+#pragma unroll
+                        for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                                const uint64_t ad = kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                                const uint64_t bd =
+                                    kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
+                                    (uint64_t)(2 * kk);
+                                tc_mma<V::KIND>(dt, ad, bd, V::IDESC, (first && kk == 0 && q == 0) ? 0u : 1u);
+                            }
+                        }
+                        tc_commit(empty0 + 8 * s);
+                        if ((kt % CKT) == CKT - 1 || kt == kt_end - 1) {
+                            tc_commit(accf0 + 8 * b);
+                            ++c;
+                        }
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
@@ -737,7 +764,13 @@ __global__ void __launch_bounds__(V::THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < COLS; j += 32) {
                     uint32_t r[32];
-                    if constexpr (V::SCALED) {
+                    if constexpr (V::MERGED) {
+                        // one accumulator: chunk sum (times the chunk's scales) into the registers
+                        tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + j), r);
+                        const float s32 = sc[V::SCALED ? j / 32 : 0];  // 1 for the unscaled kinds
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) racc[j + q] = fmaf(__uint_as_float(r[q]), s32, racc[j + q]);
+                    } else if constexpr (V::SCALED) {
                         // (left + right) * 2^-S_A * 2^-S_B (a power of two: exact),
                         // added into the FP32 registers with one rounding.
                         const float s32 = sc[j / 32];

@@ -48,7 +48,7 @@ def test_registry_rules():
         assert d["smem_bytes"] <= 232448
         if d["kind"] != 0:
             # split-precision tensor-core variants: 128-row tiles (256 for a CTA pair), TMA, any layout
-            assert d["kind"] in (1, 2, 3) and d["bn"] in (32, 64, 128)
+            assert d["kind"] in (1, 2, 3) and d["bn"] in (32, 64, 128, 256)
             assert d["bm"] == (256 if d["name"].endswith("_2sm") else 128)
             assert d["name"].startswith({1: "tc3xtf32_", 2: "tcbf16x3_", 3: "tc3xf16_"}[d["kind"]])
             # fused versions read B (or A) themselves: transB (transA) = 'N' only; the others take any layout
