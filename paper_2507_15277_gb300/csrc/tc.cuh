@@ -596,7 +596,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
 #pragma unroll
                             for (int q = 0; q < 3; ++q) {
                                 const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-                                const uint64_t ad = kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                                const uint64_t ad =
+                                    kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
                                 const uint64_t bd =
                                     kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
                                     (uint64_t)(2 * kk);
@@ -616,7 +617,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
 #pragma unroll
                             for (int q = 0; q < 3; ++q) {
                                 const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-                                const uint64_t ad = kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                                const uint64_t ad =
+                                    kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
                                 const uint64_t bd =
                                     kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
                                     (uint64_t)(2 * kk);
@@ -636,7 +638,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                                 int pa, pb;
                                 bool wide;
                                 tc_op<V::KIND>(q, pa, pb, wide);
-                                const uint64_t ad = kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
+                                const uint64_t ad =
+                                    kmajor_desc<V::SWZ>(st + pa * V::A_PLANE_BYTES) + (uint64_t)(2 * kk);
                                 const uint64_t bd =
                                     kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
                                     (uint64_t)(2 * kk);
@@ -713,7 +716,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 tc_cta_coords<V>(t, tiles_m, tiles_n, rank, sm0, sn0);
                 srow = sm0 + sub * 32 + lane;
                 sgrp = (sn0 + grp * COLS) / 32;
-                if (c0 < c1) {
+                if (!V::MERGED && c0 < c1) {
                     const int64_t gc = kt0 / CKT + c0;
                     sa_next = args.scale_a[gc * args.ld_sa + srow];
 #pragma unroll
@@ -744,7 +747,14 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 float sc[NG];
 #pragma unroll
                 for (int q = 0; q < NG; ++q) sc[q] = 1.f;
-                if constexpr (V::SCALED) {
+                if constexpr (V::SCALED && V::MERGED) {
+                    // 256-column tiles hold no scales across chunks (registers are
+                    // short there); the loads overlap the wait for the accumulator.
+                    const int64_t gc = kt0 / CKT + ch;
+                    const float sa = args.scale_a[gc * args.ld_sa + srow];
+#pragma unroll
+                    for (int q = 0; q < NG; ++q) sc[q] = sa * args.scale_b[gc * args.ld_sb + sgrp + q];
+                } else if constexpr (V::SCALED) {
                     // This chunk's scale per 32-column group; the next chunk's loads go out.
 #pragma unroll
                     for (int q = 0; q < NG; ++q) sc[q] = sa_next * sb_next[q];
@@ -763,30 +773,39 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 tc_fence_after();
 #pragma unroll
                 for (int j = 0; j < COLS; j += 32) {
-                    uint32_t r[32];
                     if constexpr (V::MERGED) {
-                        // one accumulator: chunk sum (times the chunk's scales) into the registers
-                        tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + j), r);
+                        // one accumulator: chunk sum (times the chunk's scales) into the
+                        // registers, 16 columns per load (the 128 accumulator registers
+                        // leave little room)
                         const float s32 = sc[V::SCALED ? j / 32 : 0];  // 1 for the unscaled kinds
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) racc[j + q] = fmaf(__uint_as_float(r[q]), s32, racc[j + q]);
-                    } else if constexpr (V::SCALED) {
-                        // (left + right) * 2^-S_A * 2^-S_B (a power of two: exact),
-                        // added into the FP32 registers with one rounding.
-                        const float s32 = sc[j / 32];
-                        uint32_t r2[32];
-                        tmem_ld32x2(lane_base + (uint32_t)(b * V::ACC_COLS + j),
-                                    lane_base + (uint32_t)(b * V::ACC_COLS + BN + j), r, r2);
+                        for (int h = 0; h < 32; h += 16) {
+                            uint32_t r16[16];
+                            tmem_ld16(lane_base + (uint32_t)(b * V::ACC_COLS + j + h), r16);
 #pragma unroll
-                        for (int q = 0; q < 32; ++q)
-                            racc[j + q] = fmaf(__uint_as_float(r[q]) + __uint_as_float(r2[q]), s32, racc[j + q]);
+                            for (int q = 0; q < 16; ++q)
+                                racc[j + h + q] = fmaf(__uint_as_float(r16[q]), s32, racc[j + h + q]);
+                        }
                     } else {
-                        tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + j), r);
+                        uint32_t r[32];
+                        if constexpr (V::SCALED) {
+                            // (left + right) * 2^-S_A * 2^-S_B (a power of two: exact),
+                            // added into the FP32 registers with one rounding.
+                            const float s32 = sc[j / 32];
+                            uint32_t r2[32];
+                            tmem_ld32x2(lane_base + (uint32_t)(b * V::ACC_COLS + j),
+                                        lane_base + (uint32_t)(b * V::ACC_COLS + BN + j), r, r2);
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
-                        tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + BN + j), r);
+                            for (int q = 0; q < 32; ++q)
+                                racc[j + q] = fmaf(__uint_as_float(r[q]) + __uint_as_float(r2[q]), s32, racc[j + q]);
+                        } else {
+                            tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + j), r);
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
+                            for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
+                            tmem_ld32(lane_base + (uint32_t)(b * V::ACC_COLS + BN + j), r);
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) racc[j + q] += __uint_as_float(r[q]);
+                        }
                     }
                 }
                 tc_fence_before();
