@@ -394,6 +394,7 @@ std::vector<VariantEntry> tc_variants() {
         // 256-column tiles: three N = 256 MMAs per k step into one accumulator,
         // four 48 KB stages of 64-byte rows.
         tc_entry<Tc<kTcF16s, 256, 4, 1, 64>>("tc3xf16_m128n256_p4_sw64"),
+        tc_entry<Tc<kTcF16s, 256, 4, 1, 64, 1>>("tc3xf16_m128n256_p4_sw64_stk"),
     };
 }
 
