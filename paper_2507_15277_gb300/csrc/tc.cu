@@ -80,6 +80,18 @@ int make_map_3d(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int 
 
 inline int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 
+// Number of SMs of device `dev` (cached).
+int device_sms(int dev) {
+    static std::atomic<int> sm_count[64];
+    int sms = dev >= 0 && dev < 64 ? sm_count[dev].load(std::memory_order_relaxed) : 0;
+    if (sms <= 0) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+        if (dev >= 0 && dev < 64) sm_count[dev].store(sms, std::memory_order_relaxed);
+    }
+    return sms;
+}
+
 // Pair versions: how many CTA pairs of this kernel can be resident at once
 // (clusters of two need two free SMs of one GPC), so the persistent grid is
 // a single wave.  Cached per device.
@@ -134,16 +146,14 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     // one); stream-K needs every CTA to hold at least one chunk.
     int64_t grid = tiles;
     if (V::SPLITK == 1) {
-        static std::atomic<int> sm_count[64];
-        int sms = dev < 64 ? sm_count[dev].load(std::memory_order_relaxed) : 0;
-        if (sms <= 0) {
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (sms <= 0) sms = 1;
-            if (dev < 64) sm_count[dev].store(sms, std::memory_order_relaxed);
-        }
+        const int sms = device_sms(dev);
         if (V::STREAMK) {
             const int64_t nch = (((int64_t)a.K + V::BK - 1) / V::BK + V::CHUNK_KT - 1) / V::CHUNK_KT;
             grid = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(sms, kSkMaxGrid), tiles * nch));
+            // Between 3/4 of a wave and one wave of tiles, one CTA per tile (the
+            // schedule then has no shared tiles): splitting every tile over 1-1.3
+            // CTAs costs more in partial tiles than the idle SMs do.
+            if (tiles <= sms && 4 * tiles >= 3 * (int64_t)sms) grid = tiles;
         } else if (V::PAIR) {
             // Two CTAs per tile, at most as many pairs as fit on the device at once.
             grid = 2 * std::min<int64_t>(tiles, max_pairs<V>(dev, sms));
@@ -284,6 +294,27 @@ VariantEntry tc_entry(const char *name) {
     return v;
 }
 
+// A persistent version that switches to its stream-K twin when the tiles
+// make more than one wave and the last wave is less than 3/4 full (there the
+// idle SMs of the last wave cost more than the shared tiles' partial sums);
+// single-wave and near-whole-wave shapes keep one CTA per tile.  The
+// descriptor is the persistent one's.
+template <class Vdp, class Vsk>
+int launch_tc_hybrid(const GemmArgs &a, cudaStream_t st, bool dry) {
+    const int64_t tiles = (((int64_t)a.M + Vdp::TILE_M - 1) / Vdp::TILE_M) * (((int64_t)a.N + Vdp::BN - 1) / Vdp::BN);
+    const int sms = device_sms(current_device());
+    const int64_t tail = tiles % sms;
+    const bool sk = tiles > sms && tail != 0 && 4 * tail < 3 * (int64_t)sms;
+    return sk ? launch_tc<Vsk>(a, st, dry) : launch_tc<Vdp>(a, st, dry);
+}
+
+template <class Vdp, class Vsk>
+VariantEntry tc_entry_hybrid(const char *name) {
+    VariantEntry v = tc_entry<Vdp>(name);
+    v.launch = launch_tc_hybrid<Vdp, Vsk>;
+    return v;
+}
+
 }  // namespace
 
 int stream_workspace(cudaStream_t st, size_t need, bool dry, void **out) { return workspace(st, need, dry, out); }
@@ -393,7 +424,7 @@ std::vector<VariantEntry> tc_variants() {
         tc_entry<Tc<kTcTf32, 128, 4, 1, 128, 0, 0, 1>>("tc3xtf32_m256n128_p4_2sm"),
         // 256-column tiles: three N = 256 MMAs per k step into one accumulator,
         // four 48 KB stages of 64-byte rows.
-        tc_entry<Tc<kTcF16s, 256, 4, 1, 64>>("tc3xf16_m128n256_p4_sw64"),
+        tc_entry_hybrid<Tc<kTcF16s, 256, 4, 1, 64>, Tc<kTcF16s, 256, 4, 1, 64, 1>>("tc3xf16_m128n256_p4_sw64"),
         tc_entry<Tc<kTcF16s, 256, 4, 1, 64, 1>>("tc3xf16_m128n256_p4_sw64_stk"),
     };
 }

@@ -20,7 +20,8 @@ pt = pytest.importorskip("paper_2507_15277_gb300")
 
 DEV = "cuda:0"
 STK = ["tcbf16x3_m128n128_p2_stk", "tcbf16x3_m128n128_p4_sw64_stk", "tcbf16x3_m128n64_p3_stk",
-       "tc3xtf32_m128n128_p3_stk", "tc3xtf32_m128n64_p4_stk"]
+       "tc3xtf32_m128n128_p3_stk", "tc3xtf32_m128n64_p4_stk", "tc3xf16_m128n128_p3_stk",
+       "tc3xf16_m128n256_p4_sw64_stk"]
 SHAPES = [(1024, 1024, 4096),   # 64 or 128 tiles x 32 chunks over the SMs: tiles split between CTAs
           (256, 256, 4096),     # few tiles, one chunk per CTA: many contributors per tile
           (300, 200, 1000),     # ragged edges, 8 chunks per tile
@@ -103,3 +104,49 @@ def test_streamk_after_shutdown_recreates_workspace():
         torch.cuda.synchronize()
         assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
         pt.shutdown()
+
+
+@pytest.mark.parametrize("name", STK)
+def test_streamk_whole_tiles_near_one_wave(name):
+    # Between 3/4 of a wave and a wave of tiles the launcher gives each tile
+    # its own CTA (no shared tiles); the result is the same exact integer.
+    d = pt.variant(pt.variant_by_name(name))
+    sms = torch.cuda.get_device_properties(DEV).multi_processor_count
+    rows = 12
+    cols = (sms * 9 // 10) // rows  # 0.9 of a wave of tiles
+    M, N, K = rows * d["bm"], cols * d["bn"], 520
+    A = matrix("ints", 23, M, K)
+    B = matrix("ints", 24, K, N)
+    ref = og.gemm(A, B)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    C = torch.full((M, N), float("nan"), device=DEV)
+    vid = pt.variant_by_name(name)
+    for _ in range(2):
+        C.fill_(float("nan"))
+        pt.sgemm(Ad, Bd, C, variant=vid)
+        torch.cuda.synchronize()
+        assert np.array_equal(C.cpu().numpy().astype(np.float64), ref), (name, M, N, K)
+    assert pt.device_status() == 0
+
+
+@pytest.mark.parametrize("tiles_over", [10, -20])
+def test_hybrid_wide_version_both_schedules(tiles_over):
+    # tc3xf16_m128n256_p4_sw64 runs its stream-K twin when the tiles make more
+    # than a wave with a last wave under 3/4 full (tiles_over = 10), one CTA per
+    # tile otherwise (tiles_over = -20); both give the exact integer result.
+    name = "tc3xf16_m128n256_p4_sw64"
+    sms = torch.cuda.get_device_properties(DEV).multi_processor_count
+    rows = 12
+    cols = (sms + tiles_over) // rows + 1
+    M, N, K = rows * 128, cols * 256, 520
+    A = matrix("ints", 25, M, K)
+    B = matrix("ints", 26, K, N)
+    ref = og.gemm(A, B)
+    Ad, Bd = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    C = torch.full((M, N), float("nan"), device=DEV)
+    for _ in range(2):
+        C.fill_(float("nan"))
+        pt.sgemm(Ad, Bd, C, variant=pt.variant_by_name(name))
+        torch.cuda.synchronize()
+        assert np.array_equal(C.cpu().numpy().astype(np.float64), ref), (M, N, K)
+    assert pt.device_status() == 0
