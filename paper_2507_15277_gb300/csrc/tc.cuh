@@ -168,11 +168,13 @@ struct Tc {
     static constexpr int CONV_ALL_WARPS = FUSE ? (EPI_CONV ? EPI_WARPS : 0) + CONV_WARPS : 0;
     static constexpr int CONV_THREADS = 32 * CONV_ALL_WARPS;
     // Epilogue staging (when it fits): each epilogue warp transposes its 32
-    // rows through a 32 x STG_LD float buffer, 32 columns at a time, so that
-    // C is written in whole 128-byte row segments.
+    // rows through a STG_ROWS x STG_LD float buffer, 32 columns at a time, so
+    // that C is written in whole 128-byte row segments; 16 rows at a time
+    // (two passes) where a 32-row buffer does not fit beside the pipeline.
     static constexpr int STG_LD = 36;
-    static constexpr int STG_WARP_FLOATS = 32 * STG_LD;
     static constexpr int STG_OFFSET = (BAR_OFFSET + BAR_BYTES + 15) / 16 * 16;
+    static constexpr int STG_ROWS = STG_OFFSET + EPI_WARPS * 32 * STG_LD * 4 + 1024 <= 232448 ? 32 : 16;
+    static constexpr int STG_WARP_FLOATS = STG_ROWS * STG_LD;
     static constexpr int STG_END = STG_OFFSET + EPI_WARPS * STG_WARP_FLOATS * 4;
     static constexpr bool STAGE_C = STG_END + 1024 <= 232448;
     static constexpr int SMEM_BYTES = (STAGE_C ? STG_END : STG_OFFSET) + 1024;
@@ -863,26 +865,31 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             if (V::SPLITK == 1 && epi_ok && V::STAGE_C) {
                 // Coalesced store: the warp's 32 x 32 blocks go through its
                 // staging buffer (row = lane in, four rows of 32 columns per
-                // instruction out).
+                // instruction out), STG_ROWS rows per pass.
                 int m0, n0;
                 tc_cta_coords<V>(t, tiles_m, tiles_n, rank, m0, n0);
                 float *stg = reinterpret_cast<float *>(smem_raw + (sbase - raw) + V::STG_OFFSET) +
                              warp * V::STG_WARP_FLOATS;
                 const int rr = lane >> 3, cc = (lane & 7) * 4;
                 const float as = alpha;
+                constexpr int SR = V::STG_ROWS;
 #pragma unroll
                 for (int jb = 0; jb < COLS; jb += 32) {
 #pragma unroll
-                    for (int q = 0; q < 32; q += 4)
-                        *reinterpret_cast<float4 *>(stg + lane * V::STG_LD + q) =
-                            make_float4(as * racc[jb + q], as * racc[jb + q + 1], as * racc[jb + q + 2],
-                                        as * racc[jb + q + 3]);
+                for (int h = 0; h < 32 / SR; ++h) {
+                    if (lane / SR == h) {
+#pragma unroll
+                        for (int q = 0; q < 32; q += 4)
+                            *reinterpret_cast<float4 *>(stg + (lane % SR) * V::STG_LD + q) =
+                                make_float4(as * racc[jb + q], as * racc[jb + q + 1], as * racc[jb + q + 2],
+                                            as * racc[jb + q + 3]);
+                    }
                     __syncwarp();
                     const int col = n0 + grp * COLS + jb + cc;
 #pragma unroll
-                    for (int it = 0; it < 8; ++it) {
+                    for (int it = 0; it < SR / 4; ++it) {
                         const int r = it * 4 + rr;
-                        const int row = m0 + sub * 32 + r;
+                        const int row = m0 + sub * 32 + h * SR + r;
                         float4 v = *reinterpret_cast<const float4 *>(stg + r * V::STG_LD + cc);
                         if (row < args.M && col < args.N) {
                             float *cp = args.C + (int64_t)row * args.ldc + col;
@@ -901,6 +908,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         }
                     }
                     __syncwarp();
+                }
                 }
             } else if (V::SPLITK == 1 && epi_ok) {
                 int m0, n0;
