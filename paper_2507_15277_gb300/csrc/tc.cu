@@ -148,12 +148,16 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     if (V::SPLITK == 1) {
         const int sms = device_sms(dev);
         if (V::STREAMK) {
+            // Scheduling units: CTAs, or CTA pairs (at most as many as fit at once).
             const int64_t nch = (((int64_t)a.K + V::BK - 1) / V::BK + V::CHUNK_KT - 1) / V::CHUNK_KT;
-            grid = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(sms, kSkMaxGrid), tiles * nch));
-            // Between 3/4 of a wave and one wave of tiles, one CTA per tile (the
+            const int64_t cap = V::PAIR ? std::min<int64_t>(max_pairs<V>(dev, sms), kSkMaxGrid / 2)
+                                        : std::min<int64_t>(sms, kSkMaxGrid);
+            int64_t units = std::max<int64_t>(1, std::min<int64_t>(cap, tiles * nch));
+            // Between 3/4 of a wave and one wave of tiles, one unit per tile (the
             // schedule then has no shared tiles): splitting every tile over 1-1.3
-            // CTAs costs more in partial tiles than the idle SMs do.
-            if (tiles <= sms && 4 * tiles >= 3 * (int64_t)sms) grid = tiles;
+            // units costs more in partial tiles than the idle SMs do.
+            if (tiles <= cap && 4 * tiles >= 3 * cap) units = tiles;
+            grid = (V::PAIR ? 2 : 1) * units;
         } else if (V::PAIR) {
             // Two CTAs per tile, at most as many pairs as fit on the device at once.
             grid = 2 * std::min<int64_t>(tiles, max_pairs<V>(dev, sms));
@@ -167,7 +171,10 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int64_t header = align256((int64_t)kSkHeaderBytes);
     const int64_t partials = V::STREAMK ? align256(grid * V::BM * V::BN * 4) : 0;
     const int64_t nchk = ((int64_t)a.K + V::CHUNK_K - 1) / V::CHUNK_K;
-    const int64_t ld_sa = ((int64_t)a.M + V::TILE_M - 1) / V::TILE_M * V::TILE_M, ld_sb = ((int64_t)a.N + 127) / 128 * 4;
+    // (every tile's rows and 32-column groups have a slot, also past M and N)
+    constexpr int64_t NR = V::BN > 128 ? V::BN : 128;
+    const int64_t ld_sa = ((int64_t)a.M + V::TILE_M - 1) / V::TILE_M * V::TILE_M,
+                  ld_sb = ((int64_t)a.N + NR - 1) / NR * (NR / 32);
     const int64_t sa_bytes = V::SCALED ? align256(nchk * ld_sa * 4) : 0;
     const int64_t sb_bytes = V::SCALED ? align256(nchk * ld_sb * 4) : 0;
     const size_t need =
@@ -302,9 +309,10 @@ VariantEntry tc_entry(const char *name) {
 template <class Vdp, class Vsk>
 int launch_tc_hybrid(const GemmArgs &a, cudaStream_t st, bool dry) {
     const int64_t tiles = (((int64_t)a.M + Vdp::TILE_M - 1) / Vdp::TILE_M) * (((int64_t)a.N + Vdp::BN - 1) / Vdp::BN);
-    const int sms = device_sms(current_device());
-    const int64_t tail = tiles % sms;
-    const bool sk = tiles > sms && tail != 0 && 4 * tail < 3 * (int64_t)sms;
+    const int dev = current_device(), sms = device_sms(dev);
+    const int64_t cap = Vdp::PAIR ? max_pairs<Vdp>(dev, sms) : sms;  // tiles in flight at once
+    const int64_t tail = tiles % cap;
+    const bool sk = tiles > cap && tail != 0 && 4 * tail < 3 * cap;
     return sk ? launch_tc<Vsk>(a, st, dry) : launch_tc<Vdp>(a, st, dry);
 }
 
@@ -426,6 +434,15 @@ std::vector<VariantEntry> tc_variants() {
         // four 48 KB stages of 64-byte rows.
         tc_entry_hybrid<Tc<kTcF16s, 256, 4, 1, 64>, Tc<kTcF16s, 256, 4, 1, 64, 1>>("tc3xf16_m128n256_p4_sw64"),
         tc_entry<Tc<kTcF16s, 256, 4, 1, 64, 1>>("tc3xf16_m128n256_p4_sw64_stk"),
+        // 256 x 256 pair tiles: each CTA loads its 128 rows of A and 128 of the
+        // 256 rows of op(B)^T (32 KB stages of 64-byte rows); three N = 256
+        // MMAs of M = 256 per k step into one accumulator; stream-K per pair
+        // when the last wave of pairs is under 3/4 full.
+        tc_entry_hybrid<Tc<kTcF16s, 256, 6, 1, 64, 0, 0, 1>, Tc<kTcF16s, 256, 6, 1, 64, 1, 0, 1>>(
+            "tc3xf16_m256n256_p6_sw64_2sm"),
+        tc_entry<Tc<kTcF16s, 256, 6, 1, 64, 1, 0, 1>>("tc3xf16_m256n256_p6_sw64_2sm_stk"),
+        tc_entry_hybrid<Tc<kTcF16s, 256, 5, 1, 64, 0, 0, 1>, Tc<kTcF16s, 256, 5, 1, 64, 1, 0, 1>>(
+            "tc3xf16_m256n256_p5_sw64_2sm"),
     };
 }
 

@@ -85,22 +85,23 @@ struct Tc {
     static_assert(FUSE == 0 || KIND_ == kTcBf16x3, "fused split is BF16x3 only");
     // Two-CTA pair (cta_group::2): a cluster (2,1,1) computes 256 x BN tiles
     // with M = 256 MMAs that its even CTA issues.  Each CTA loads its 128 rows
-    // of A and half of the tile's BN rows of op(B)^T, so a stage holds 3/4 of
-    // the bytes of a one-CTA stage for the same MMA work per SM and one more
-    // stage fits.  The products are not paired along N (three N = BN MMAs per
-    // k step): the two halves of B sit in different CTAs.
+    // of A and half of the tile's BN rows of op(B)^T, so a stage holds 3/4
+    // (BN = 128) or 2/3 (BN = 256) of the bytes of a one-CTA stage for the
+    // same MMA work per SM, and more stages fit.  The products are not paired
+    // along N (three N = BN MMAs per k step): the two halves of B sit in
+    // different CTAs.  Stream-K pairs share chunks per CTA pair.
     static constexpr bool PAIR = PAIR_ != 0;
-    static_assert(!PAIR || (SPLITK_ == 1 && STREAMK_ == 0 && FUSE_ == 0 && BN_ == 128 && KIND_ != kTcBf16x3),
-                  "pair versions: persistent, unfused, 128 columns, three products");
+    static_assert(!PAIR || (SPLITK_ == 1 && FUSE_ == 0 && (BN_ == 128 || BN_ == 256) && KIND_ != kTcBf16x3),
+                  "pair versions: unfused, 128 or 256 columns, three products");
     static constexpr int TILE_M = PAIR ? 256 : 128;  // rows of a scheduled tile
-    // 256-column tiles (three-product kinds, one CTA): every product is one
-    // N = 256 MMA into a single accumulator of 256 columns (no left / right
-    // halves), so a k step is three MMAs for twice the output of a 128-column
-    // tile's two (N = 256 + N = 128), and the two buffers still fit tensor
-    // memory.
+    // 256-column tiles (three-product kinds, one CTA or a pair): every
+    // product is one N = 256 MMA into a single accumulator of 256 columns (no
+    // left / right halves), so a k step is three MMAs for twice the output of
+    // a 128-column tile's two (N = 256 + N = 128), and the two buffers still
+    // fit tensor memory.
     static constexpr bool MERGED = BN_ == 256;
-    static_assert(!MERGED || (KIND_ != kTcBf16x3 && FUSE_ == 0 && !PAIR && SPLITK_ == 1),
-                  "256-column tiles: three-product kinds, unfused, one CTA, no split-K");
+    static_assert(!MERGED || (KIND_ != kTcBf16x3 && FUSE_ == 0 && SPLITK_ == 1),
+                  "256-column tiles: three-product kinds, unfused, no split-K");
     static constexpr int B_ROWS = PAIR ? BN_ / 2 : BN_;  // rows of op(B)^T a CTA loads per tile
     // Bytes of k per tile row = the TMA / MMA swizzle span (128, 64 or 32).
     // A narrower row makes the stage smaller, so more stages fit and the
@@ -453,14 +454,17 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     work.tiles = tiles;
     work.streamk = V::STREAMK != 0;
     // Stream-K: whole tiles for all but the last full wave, then the rest
-    // (one to two waves' worth) shared in chunks.
-    const int G = (int)gridDim.x;
+    // (one to two waves' worth) shared in chunks.  The scheduling unit is a
+    // CTA, or a CTA pair in pair versions (both CTAs of a pair have the same
+    // work; each keeps its own partial-tile slot, blockIdx.x).
+    const int G = V::PAIR ? (int)gridDim.x / 2 : (int)gridDim.x;
+    const int unit = t_first;
     const int full_waves = tiles / G;
     work.ndp = full_waves >= 2 ? full_waves - 1 : 0;
     work.sk_tile0 = work.ndp * G;
     const int64_t W_sk = (int64_t)(tiles - work.sk_tile0) * nchunks;
-    work.lo = (int64_t)blockIdx.x * W_sk / G;
-    work.hi = ((int64_t)blockIdx.x + 1) * W_sk / G;
+    work.lo = (int64_t)unit * W_sk / G;
+    work.hi = ((int64_t)unit + 1) * W_sk / G;
     const int nseg = work.count();
 
     if (tid == 0) {
@@ -592,7 +596,8 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     const uint32_t st = sbase + s * V::STAGE_BYTES;
                     const uint32_t dt = tmem + (uint32_t)(b * V::ACC_COLS);
                     if constexpr (V::PAIR) {
-                        // A0 B0 into the left half; A0 B1 and A1 B0 into the right half.
+                        // A0 B0 into the left half; A0 B1 and A1 B0 into the right half
+                        // (256-column pairs: all three into the one accumulator).
 #pragma unroll
                         for (int kk = 0; kk < BK / V::KSTEP; ++kk) {
 #pragma unroll
@@ -603,8 +608,9 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                                 const uint64_t bd =
                                     kmajor_desc<V::SWZ>(st + P * V::A_PLANE_BYTES + pb * V::B_PLANE_BYTES) +
                                     (uint64_t)(2 * kk);
-                                tc_mma_pair<V::KIND>(q == 0 ? dt : dt + (uint32_t)BN, ad, bd, V::IDESC,
-                                                     (first && kk == 0 && q < 2) ? 0u : 1u);
+                                const bool zero = first && kk == 0 && (V::MERGED ? q == 0 : q < 2);
+                                tc_mma_pair<V::KIND>((V::MERGED || q == 0) ? dt : dt + (uint32_t)BN, ad, bd, V::IDESC,
+                                                     zero ? 0u : 1u);
                             }
                         }
                         tc_commit_pair(empty0 + 8 * s);
@@ -838,12 +844,14 @@ __global__ void __launch_bounds__(V::THREADS, 1)
             if (V::STREAMK != 0 && epi_ok && c0 > 0) {
                 // Finisher: add the partial tiles of the earlier CTAs that
                 // share this tile (nearest first), after their flags are set.
+                // (pair versions: the same-rank CTA of each earlier pair)
                 const int64_t tile_lo = (int64_t)(t - work.sk_tile0) * nchunks;
-                for (int j = (int)blockIdx.x - 1; j >= 0; --j) {
+                for (int j = unit - 1; j >= 0; --j) {
                     const int64_t lo_j = (int64_t)j * W_sk / G, hi_j = ((int64_t)j + 1) * W_sk / G;
                     if (hi_j <= tile_lo) break;
                     if (lo_j == hi_j) continue;  // an empty range contributes nothing
-                    const unsigned *flag = args.sk_words + kSkFlags + kSkFlagsPerCta * j + warp;
+                    const int slot = V::PAIR ? 2 * j + (int)rank : j;
+                    const unsigned *flag = args.sk_words + kSkFlags + kSkFlagsPerCta * slot + warp;
                     const uint64_t t0 = globaltimer_ns();
                     bool ready = false;
                     while (!(ready = ld_acquire_u32(flag) == epoch1 + args.sk_wait_bias)) {
@@ -854,7 +862,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                         break;
                     }
                     const float4 *pr = reinterpret_cast<const float4 *>(args.sk_partials) +
-                                       ((int64_t)j * V::EPI_WARPS + warp) * (COLS / 4) * 32 + lane;
+                                       ((int64_t)slot * V::EPI_WARPS + warp) * (COLS / 4) * 32 + lane;
 #pragma unroll
                     for (int q = 0; q < COLS; q += 4) {
                         const float4 v = pr[(q / 4) * 32];

@@ -1,13 +1,17 @@
 """GPU: the two-CTA (cta_group::2) tensor-core versions.
 
-A cluster of two CTAs computes a 256 x 128 tile: each CTA loads its 128 rows
-of A and half of the tile's columns of B, the even CTA issues M = 256 MMAs
-over both CTAs' shared memory, and each CTA drains its own rows from its own
-tensor memory.  These tests hold the pair versions to the FP64 oracle where
-the pairing can go wrong: row tiles whose second half lies partly or wholly
-past M (the odd CTA then loads zero rows and stores nothing), N not a
-multiple of the per-CTA half, more tiles than resident pairs, every
-transpose pair, alpha/beta, and the all-plane exact pins of the split.
+A cluster of two CTAs computes a 256 x 128 or 256 x 256 tile: each CTA loads
+its 128 rows of A and half of the tile's columns of B, the even CTA issues
+M = 256 MMAs over both CTAs' shared memory, and each CTA drains its own rows
+from its own tensor memory.  These tests hold the pair versions to the FP64
+oracle where the pairing can go wrong: row tiles whose second half lies
+partly or wholly past M (the odd CTA then loads zero rows and stores
+nothing), N not a multiple of the per-CTA half, more tiles than resident
+pairs, every transpose pair, alpha/beta, and the all-plane exact pins of the
+split.  The 256-column pairs also run stream-K over CTA pairs (each CTA of a
+finishing pair adds the partial tiles of the same-rank CTAs of earlier
+pairs): the `_stk` version always, the hybrid when the last wave of pair
+tiles is under 3/4 full.
 """
 
 import numpy as np
@@ -22,7 +26,8 @@ torch = pytest.importorskip("torch")
 pt = pytest.importorskip("paper_2507_15277_gb300")
 
 DEV = "cuda:0"
-PAIRS = ("tc3xf16_m256n128_p4_2sm", "tc3xtf32_m256n128_p4_2sm")
+PAIRS = ("tc3xf16_m256n128_p4_2sm", "tc3xtf32_m256n128_p4_2sm", "tc3xf16_m256n256_p6_sw64_2sm",
+         "tc3xf16_m256n256_p5_sw64_2sm", "tc3xf16_m256n256_p6_sw64_2sm_stk")
 
 
 def _vid(name):
@@ -40,7 +45,10 @@ def _run(name, A, B, M, N, ta="N", tb="N", alpha=1.0, beta=0.0, C0=None):
 def test_pair_versions_registered():
     for name in PAIRS:
         d = pt.variant(_vid(name))
-        assert d["bm"] == 256 and d["bn"] == 128 and d["stages"] == 4 and d["trans_mask"] == 15
+        bn = 256 if "n256" in name else 128
+        assert d["bm"] == 256 and d["bn"] == bn and d["trans_mask"] == 15
+        assert d["stages"] == int(name.split("_p")[1].split("_")[0])
+        assert d["schedule"] == (pt.PT_SCHED_STREAMK if name.endswith("_stk") else pt.PT_SCHED_PERSISTENT)
 
 
 @pytest.mark.parametrize("name", PAIRS)
@@ -92,4 +100,18 @@ def test_pair_alpha_beta(name):
     ref = og.gemm(A, B, alpha=0.75, beta=-1.5, C=C0)
     out = _run(name, A, B, M, N, alpha=0.75, beta=-1.5, C0=C0)
     assert np.abs(out - ref).max() <= 2e-6 * (K * 0.75 + 1.5), name
+    assert pt.device_status() == 0
+
+
+@pytest.mark.parametrize("name", ["tc3xf16_m256n256_p6_sw64_2sm", "tc3xf16_m256n256_p5_sw64_2sm"])
+def test_pair_hybrid_streamk_tail(name):
+    # 10 x 10 = 100 pair tiles: more than the resident pairs, with a last wave
+    # under 3/4 full, so the hybrid runs its stream-K pair instantiation;
+    # repeated launches must not read earlier launches' partial tiles.
+    M, N, K = 2560, 2560, 1024
+    A, B, _ = wide_int_operands(19, M, N, K)
+    ref = og.gemm(A, B)
+    for _ in range(3):
+        out = _run(name, A, B, M, N)
+        assert np.array_equal(out.astype(np.float64), ref), name
     assert pt.device_status() == 0

@@ -21,7 +21,7 @@ pt = pytest.importorskip("paper_2507_15277_gb300")
 DEV = "cuda:0"
 STK = ["tcbf16x3_m128n128_p2_stk", "tcbf16x3_m128n128_p4_sw64_stk", "tcbf16x3_m128n64_p3_stk",
        "tc3xtf32_m128n128_p3_stk", "tc3xtf32_m128n64_p4_stk", "tc3xf16_m128n128_p3_stk",
-       "tc3xf16_m128n256_p4_sw64_stk"]
+       "tc3xf16_m128n256_p4_sw64_stk", "tc3xf16_m256n256_p6_sw64_2sm_stk"]
 SHAPES = [(1024, 1024, 4096),   # 64 or 128 tiles x 32 chunks over the SMs: tiles split between CTAs
           (256, 256, 4096),     # few tiles, one chunk per CTA: many contributors per tile
           (300, 200, 1000),     # ragged edges, 8 chunks per tile
