@@ -193,7 +193,9 @@ struct Tc {
     static_assert(BM % SPLITK == 0, "split-K reduction slices rows");
     // Consecutive CTAs walk GROUP_M tile rows down before moving right, so a
     // wave's A and B panels stay in L2.
-    static constexpr int GROUP_M = PAIR ? 4 : 8;
+    // (256 x 256 pair tiles: 8 rows of pairs, about the square root of the
+    // pairs in a wave, which minimises the A and B panels a wave reads.)
+    static constexpr int GROUP_M = PAIR && !MERGED ? 4 : 8;
     static_assert(TMEM_COLS <= 512, "tensor memory columns");
     static_assert(EPI_WARPS <= 8, "stream-K flag slots per CTA");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
