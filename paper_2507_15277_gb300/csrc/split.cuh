@@ -233,8 +233,12 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, con
     const int r = r0 + (tid >> 3), kt8 = (tid & 7) * 8;
     float x[SPLIT_KT][8];
     // Launched with programmatic stream serialization: the previous kernel
-    // (e.g. a GEMM still reading the planes) completes first.
+    // (e.g. a GEMM still reading the planes) completes first.  The GEMM that
+    // reads these planes may be scheduled as soon as every block of this grid
+    // has started (it waits for this grid to complete before it reads them),
+    // so its launch and prologue overlap this grid's last wave.
     pdl_wait();
+    pdl_trigger();
     split_load_block(o, K, r0, kb, tid, x, tile);
     if constexpr (KIND == kTcF16s) {
         // The block's 256 values of k are chunk blockIdx.x.  First operand:
@@ -272,7 +276,6 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const SplitOperand a, con
         const int k = kb + 64 * t + kt8;
         if (r < o.rows && k < pitch) split_store8<KIND>(o.ws, o.plane_bytes, pitch, r, k, x[t]);
     }
-    pdl_trigger();
 }
 
 }  // namespace pt

@@ -565,6 +565,10 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 }
             }
             s_issued = g;
+            // Every load of this CTA is issued: the next kernel of the stream
+            // may be scheduled (on SMs this grid leaves free; it waits for this
+            // grid to complete before it touches memory).
+            pdl_trigger();
         }
     } else if (warp == V::MMA_WARP) {
         if (lane == 0 && rank == 0) {  // pair versions: the even CTA issues for both
