@@ -144,10 +144,12 @@ int pt_variant_by_name(const char *name);
  * largest |a| of the row times the largest |b| of the column's group.  It
  * gives that accuracy while those maxima lie in [2^-49, 2^78]; larger values
  * overflow FP16 (C gets Inf or
- * NaN) and smaller ones keep fewer bits.  Names ending in "_2sm" run a
- * cluster of two CTAs per 256 x 128 tile with cta_group::2 MMAs of M = 256
- * (each CTA loads its 128 rows of A and half of the tile's B); names with
- * "n256" compute 128 x 256 tiles whose three products accumulate in one
+ * NaN) and smaller ones keep fewer bits.  Names with "_2sm" run a cluster
+ * of two CTAs per 256 x 128 or 256 x 256 tile with cta_group::2 MMAs of
+ * M = 256 (each CTA loads its 128 rows of A and half of the tile's B; the
+ * 256 x 256 ones run stream-K over CTA pairs when the last wave of pair
+ * tiles is under 3/4 full, always with "_stk"); names with "n256" compute
+ * 128 x 256 or 256 x 256 tiles whose three products accumulate in one
  * tensor-memory accumulator.  The paper has no tensor-core versions; they
  * are further members of the same variant space. */
 /* the fixed default variant (128x128x8 CTA tile, cp.async, any layout) */
