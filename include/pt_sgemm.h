@@ -367,6 +367,20 @@ int pt_device_status(void);
  * that inter-CTA wait is affected; the pipeline's own waits keep 2 s. */
 int pt_debug_streamk_wait(uint64_t limit_ns, int never_ready);
 
+/* Stream-K work partition (a testing aid; the paper has no counterpart): the
+ * segments that scheduling unit `unit` (a CTA, or a CTA pair in pair
+ * versions) of `units` processes when `tiles` output tiles of `nchunks`
+ * k-chunks each are shared stream-K style, computed by the same code the
+ * kernels run.  Each segment is three ints in `out` (host memory, caller
+ * owned): tile index, first chunk, end chunk (exclusive), in the order the
+ * unit visits them.  A unit first takes whole tiles unit, unit + units, ...
+ * for all but the last full wave of tiles, then an equal contiguous range of
+ * the remaining tiles x chunks, visited from its last tile to its first.
+ * Returns the number of segments (only the first `cap` are written), or
+ * PT_EINVAL for tiles, nchunks < 1, units outside [1, 2048], unit outside
+ * [0, units), cap < 0 or out == NULL with cap > 0.  No device work. */
+int pt_debug_streamk_segments(int tiles, int nchunks, int units, int unit, int *out, int cap);
+
 /* Kernel timer (a measurement aid; the paper has no counterpart).  While it
  * runs on the calling host thread, every pt_sgemm / pt_sgemm_variant call
  * records a pair of CUDA events on its stream directly around its main GEMM

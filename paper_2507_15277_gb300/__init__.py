@@ -158,6 +158,17 @@ def debug_streamk_wait(limit_ns: int = 0, never_ready: bool = False) -> None:
     _lib.check(_l().pt_debug_streamk_wait(int(limit_ns), int(bool(never_ready))), "pt_debug_streamk_wait")
 
 
+def streamk_segments(tiles: int, nchunks: int, units: int, unit: int) -> list:
+    """The (tile, first chunk, end chunk) segments stream-K unit `unit` of
+    `units` processes, in its visiting order (the kernels' own partition)."""
+    n = _l().pt_debug_streamk_segments(tiles, nchunks, units, unit, None, 0)
+    _lib.check(min(n, 0), "pt_debug_streamk_segments")
+    buf = (ctypes.c_int * max(3, 3 * n))()
+    _lib.check(min(_l().pt_debug_streamk_segments(tiles, nchunks, units, unit, buf, n), 0),
+               "pt_debug_streamk_segments")
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]
+
+
 def kernel_timer_start() -> None:
     """Starts timing the main GEMM kernel of every sgemm call on this thread."""
     _lib.check(_l().pt_kernel_timer_start(), "pt_kernel_timer_start")

@@ -102,6 +102,8 @@ SIGNATURES = {
     "pt_kernel_timer_stop": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "pt_sgemm_3xtf32_noalloc": (ctypes.c_int, _GEMM_ARGS),
     "pt_debug_streamk_wait": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    "pt_debug_streamk_segments": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "pt_grouped_plan": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int]),
     "pt_sgemm_grouped": (ctypes.c_int, [ctypes.POINTER(Problem), _p, ctypes.c_int, _p]),
 }

@@ -351,6 +351,18 @@ int pt_debug_streamk_wait(uint64_t limit_ns, int never_ready) {
     return PT_OK;
 }
 
+int pt_debug_streamk_segments(int tiles, int nchunks, int units, int unit, int *out, int cap) {
+    clear_error();
+    if (tiles < 1) return set_error(PT_EINVAL, 1, "tiles must be at least 1");
+    if (nchunks < 1) return set_error(PT_EINVAL, 2, "nchunks must be at least 1");
+    constexpr int kMaxUnits = 2048;  // the stream-K header's flag slots (kSkMaxGrid in tc.cuh)
+    if (units < 1 || units > kMaxUnits) return set_error(PT_EINVAL, 3, "units must be in [1, %d]", kMaxUnits);
+    if (unit < 0 || unit >= units) return set_error(PT_EINVAL, 4, "unit must be in [0, units)");
+    if (cap < 0 || (cap > 0 && out == nullptr)) return set_error(PT_EINVAL, 6, "out must hold cap triples");
+    if ((int64_t)tiles * nchunks > 0x7fffffffLL) return set_error(PT_EINVAL, 2, "tiles x nchunks too large");
+    return streamk_segments(tiles, nchunks, units, unit, out, cap);
+}
+
 int pt_kernel_timer_start(void) {
     clear_error();
     KernelTimer &t = kernel_timer();

@@ -38,6 +38,11 @@ int *err_word(int dev);
 // checks without allocating.
 int stream_workspace(cudaStream_t st, size_t need, bool dry, void **out);
 
+// The stream-K segments (tile, first chunk, end chunk) of unit `unit` of
+// `units` over tiles x nchunks, from the kernels' own partition code (tc.cu,
+// pt_debug_streamk_segments): their number; at most `cap` are written.
+int streamk_segments(int tiles, int nchunks, int units, int unit, int *out, int cap);
+
 // Stream-K finisher wait settings for the next launches (api.cu,
 // pt_debug_streamk_wait): time limit in ns and the awaited-value offset.
 void streamk_wait_settings(uint64_t *limit_ns, unsigned *bias);

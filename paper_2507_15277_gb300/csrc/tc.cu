@@ -327,6 +327,22 @@ VariantEntry tc_entry_hybrid(const char *name) {
 
 int stream_workspace(cudaStream_t st, size_t need, bool dry, void **out) { return workspace(st, need, dry, out); }
 
+// The segments (tile, first chunk, end chunk) that stream-K unit `unit` of
+// `units` processes, in the kernel's order, from the kernel's own partition
+// code (TcWork); returns their number, writing at most `cap`.
+int streamk_segments(int tiles, int nchunks, int units, int unit, int *out, int cap) {
+    TcWork w;
+    w.nch = nchunks;
+    w.t_first = unit;
+    w.t_step = units;
+    w.tiles = tiles;
+    w.streamk = true;
+    w.streamk_init(units, unit);
+    const int n = w.count();
+    for (int i = 0; i < n && i < cap; ++i) w.seg(i, out[3 * i], out[3 * i + 1], out[3 * i + 2]);
+    return n;
+}
+
 // Tensor-core variants appended to the registry after the SIMT family.
 std::vector<VariantEntry> tc_variants() {
     return {

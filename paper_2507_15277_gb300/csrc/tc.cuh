@@ -283,11 +283,23 @@ struct TcWork {
     bool streamk;
     int ndp, sk_tile0;  // stream-K: whole tiles per CTA; first tile of the shared part
     int64_t lo, hi;     // stream-K: chunk range within the shared part
-    __device__ int count() const {
+    // Stream-K share of unit `unit` of G (a unit is a CTA, or a CTA pair):
+    // whole tiles for all but the last full wave, then the rest (one to two
+    // waves' worth) cut into G equal contiguous chunk ranges.  nch and tiles
+    // are set first.
+    __host__ __device__ void streamk_init(int G, int unit) {
+        const int full_waves = tiles / G;
+        ndp = full_waves >= 2 ? full_waves - 1 : 0;
+        sk_tile0 = ndp * G;
+        const int64_t W = (int64_t)(tiles - sk_tile0) * nch;
+        lo = (int64_t)unit * W / G;
+        hi = ((int64_t)unit + 1) * W / G;
+    }
+    __host__ __device__ int count() const {
         if (streamk) return ndp + (hi > lo ? (int)((hi - 1) / nch - lo / nch + 1) : 0);
         return t_first < tiles ? (tiles - 1 - t_first) / t_step + 1 : 0;
     }
-    __device__ void seg(int i, int &t, int &c0, int &c1) const {
+    __host__ __device__ void seg(int i, int &t, int &c0, int &c1) const {
         if (!streamk || i < ndp) {
             t = t_first + i * t_step;
             c0 = 0;
@@ -455,18 +467,13 @@ __global__ void __launch_bounds__(V::THREADS, 1)
     work.t_step = V::SPLITK > 1 ? tiles : (V::PAIR ? (int)gridDim.x / 2 : (int)gridDim.x);  // split-K: one tile
     work.tiles = tiles;
     work.streamk = V::STREAMK != 0;
-    // Stream-K: whole tiles for all but the last full wave, then the rest
-    // (one to two waves' worth) shared in chunks.  The scheduling unit is a
-    // CTA, or a CTA pair in pair versions (both CTAs of a pair have the same
-    // work; each keeps its own partial-tile slot, blockIdx.x).
+    // Stream-K: the scheduling unit is a CTA, or a CTA pair in pair versions
+    // (both CTAs of a pair have the same work; each keeps its own
+    // partial-tile slot, blockIdx.x).
     const int G = V::PAIR ? (int)gridDim.x / 2 : (int)gridDim.x;
     const int unit = t_first;
-    const int full_waves = tiles / G;
-    work.ndp = full_waves >= 2 ? full_waves - 1 : 0;
-    work.sk_tile0 = work.ndp * G;
+    work.streamk_init(G, unit);
     const int64_t W_sk = (int64_t)(tiles - work.sk_tile0) * nchunks;
-    work.lo = (int64_t)unit * W_sk / G;
-    work.hi = ((int64_t)unit + 1) * W_sk / G;
     const int nseg = work.count();
 
     if (tid == 0) {
