@@ -15,6 +15,7 @@ namespace pt {
 
 // Error reporting shared by the library's translation units (api.cu).
 int set_error(int code, int arg, const char *fmt, ...);
+void clear_error();
 
 // cuTensorMapEncodeTiled from the driver, resolved once (no libcuda link).
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,

@@ -199,6 +199,7 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     t.alpha = alpha;
     t.beta = beta;
     t.vec4 = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
+    t.tma_c = 0;  // the epilogue warps store C themselves (same values as through the TMA engine)
     t.err = err_word(dev);  // a file-scope device word as well: no allocation
     t.sk_words = nullptr;  // no stream-K in this entry point
     t.sk_partials = nullptr;
@@ -220,7 +221,7 @@ extern "C" int pt_sgemm_3xtf32_noalloc(char transA, char transB, int64_t M, int6
     cfg.stream = st;
     cfg.attrs = pdl;
     cfg.numAttrs = npdl;
-    e = cudaLaunchKernelEx(&cfg, tc_sgemm_kernel<NoAllocCfg>, t, mA, mB);
+    e = cudaLaunchKernelEx(&cfg, tc_sgemm_kernel<NoAllocCfg>, t, mA, mB, mA);  // (no C map: tma_c = 0)
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "tensor-core kernel: %s", cudaGetErrorString(e));
     return PT_OK;
 }

@@ -244,6 +244,19 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     t.alpha = a.alpha;
     t.beta = a.beta;
     t.vec4 = (!misaligned(a.C, 16) && a.ldc % 4 == 0) ? 1 : 0;
+    // C through the TMA engine where the version has the staging boxes, C
+    // need not be read (beta = 0), C and ldc are 16-byte aligned and the rows
+    // end on a 16-byte boundary (N % 4 == 0: a store of a box that crosses N
+    // wrote the rest of the row's last 16 bytes, past N); otherwise the
+    // epilogue warps store C themselves.
+    CUtensorMap mC = mA;  // unused unless tma_c
+    t.tma_c = 0;
+    if (V::TSTG_BUFS > 0 && a.beta == 0.f && t.vec4 && a.N % 4 == 0 && a.M > 0 && a.N > 0) {
+        if (make_map_2d(&mC, a.C, a.N, a.M, a.ldc, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B) == PT_OK)
+            t.tma_c = 1;
+        else
+            clear_error();
+    }
     t.err = a.err;
     t.sk_words = static_cast<unsigned *>(ws);
     t.sk_partials = reinterpret_cast<float *>(static_cast<unsigned char *>(ws) + header);
@@ -271,7 +284,7 @@ int launch_tc(const GemmArgs &a, cudaStream_t st, bool dry) {
     cfg.attrs = attr;
     cfg.numAttrs = nattr;
     kernel_timer_mark(st, true);
-    e = cudaLaunchKernelEx(&cfg, tc_sgemm_kernel<V>, t, mA, mB);
+    e = cudaLaunchKernelEx(&cfg, tc_sgemm_kernel<V>, t, mA, mB, mC);
     kernel_timer_mark(st, false);
     if (e != cudaSuccess) return set_error(PT_ECUDA, 0, "tensor-core kernel: %s", cudaGetErrorString(e));
     return PT_OK;

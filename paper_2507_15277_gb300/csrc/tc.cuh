@@ -178,7 +178,20 @@ struct Tc {
     static constexpr int STG_WARP_FLOATS = STG_ROWS * STG_LD;
     static constexpr int STG_END = STG_OFFSET + EPI_WARPS * STG_WARP_FLOATS * 4;
     static constexpr bool STAGE_C = STG_END + 1024 <= 232448;
-    static constexpr int SMEM_BYTES = (STAGE_C ? STG_END : STG_OFFSET) + 1024;
+    // TMA-store staging (SPLITK == 1, beta = 0, C 16-byte aligned): per
+    // epilogue warp TSTG_BUFS buffers holding one 32 x 32 FP32 box of C in the
+    // 128-byte swizzled layout (1024-byte aligned), two where they fit, so the
+    // warp fills one while the TMA engine still reads the other.  It shares
+    // the region after the barriers with the padded staging buffers above (a
+    // launch uses one of the two).
+    static constexpr int TSTG_OFFSET = (BAR_OFFSET + BAR_BYTES + 1023) / 1024 * 1024;
+    static constexpr int TSTG_BUFS = SPLITK_ != 1                                              ? 0
+                                     : TSTG_OFFSET + EPI_WARPS * 2 * 4096 + 1024 <= 232448 ? 2
+                                     : TSTG_OFFSET + EPI_WARPS * 4096 + 1024 <= 232448     ? 1
+                                                                                           : 0;
+    static constexpr int TSTG_END = TSTG_OFFSET + EPI_WARPS * TSTG_BUFS * 4096;
+    static constexpr int STG_USED = STAGE_C ? STG_END : STG_OFFSET;
+    static constexpr int SMEM_BYTES = (STG_USED > TSTG_END ? STG_USED : TSTG_END) + 1024;
     // Instruction descriptor: D = F32 (bits 4-5 = 1), A/B format (bits 7-9,
     // 10-12: TF32 = 2, BF16 = 1, F16 = 0), both K-major (bits 15, 16 = 0),
     // N >> 3 at bit 17, M >> 4 at bit 24.
@@ -238,12 +251,30 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
            ((uint64_t)1 << 46) | (layout << 61);
 }
 
+// TMA tile store of a 2-D box from shared memory (tracked per issuing
+// thread in bulk groups), and the waits for those groups: `.read` until the
+// shared memory of all but the newest N groups has been read, plain until
+// their global writes are done.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 struct TcArgs {
     float *C;
     int64_t ldc;
     int M, N, K;
     float alpha, beta;
     int vec4;  // C and ldc allow 16-byte stores
+    int tma_c;  // C is stored through mapC by the TMA engine (beta = 0, C and ldc 16-byte aligned)
     int *err;
     // Stream-K: words[0] = launches completed on this workspace (the epoch),
     // words[1] = CTAs of this launch that have finished, words[kSkFlags + 8b
@@ -426,7 +457,7 @@ __device__ __forceinline__ void tc_cta_coords(int t, int tiles_m, int tiles_n, u
 template <class V>
 __global__ void __launch_bounds__(V::THREADS, 1)
     tc_sgemm_kernel(const TcArgs args, const __grid_constant__ CUtensorMap mapA,
-                    const __grid_constant__ CUtensorMap mapB) {
+                    const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapC) {
     constexpr int STAGES = V::STAGES, BK = V::BK, BN = V::BN, P = V::P, CKT = V::CHUNK_KT, COLS = V::COLS;
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_fail, s_issued, s_consumed, s_peer_issued;
@@ -719,6 +750,7 @@ __global__ void __launch_bounds__(V::THREADS, 1)
         int c = 0;  // chunks drained (all segments)
         int g = 0;  // k-tiles converted (fused versions)
         unsigned epoch1 = 0;  // stream-K: this launch's flag value
+        int sblk = 0;         // C boxes handed to the TMA engine (TMA-store epilogue)
         if constexpr (V::STREAMK != 0) epoch1 = ld_acquire_u32(args.sk_words) + 1u;
         for (int i = 0; epi_ok && i < nseg; ++i) {
             int t, c0, c1;
@@ -883,7 +915,39 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                     }
                 }
             }
-            if (V::SPLITK == 1 && epi_ok && V::STAGE_C) {
+            if (V::SPLITK == 1 && V::TSTG_BUFS > 0 && epi_ok && args.tma_c) {
+                // Asynchronous store: the warp writes each 32 x 32 block (alpha
+                // applied; row = lane, 16-byte chunk q of a row at chunk
+                // q ^ (row & 7), the 128-byte swizzle of mapC) into a staging
+                // box, and one lane hands the box to the TMA engine, which clips
+                // rows and columns past M and N.  The warp goes on to its next
+                // drain while C is written.
+                int m0, n0;
+                tc_cta_coords<V>(t, tiles_m, tiles_n, rank, m0, n0);
+                constexpr int NB = V::TSTG_BUFS;
+                float *tbox = reinterpret_cast<float *>(smem_raw + (sbase - raw) + V::TSTG_OFFSET) + warp * NB * 1024;
+                const uint32_t tbox_s = sbase + V::TSTG_OFFSET + (uint32_t)(warp * NB * 4096);
+                const float as = alpha;
+#pragma unroll
+                for (int jb = 0; jb < COLS; jb += 32, ++sblk) {
+                    const int bi = sblk % NB;
+                    // the box stored NB blocks ago has been read out of buffer bi
+                    if (lane == 0) bulk_wait_read<NB - 1>();
+                    __syncwarp();
+                    float *row = tbox + bi * 1024 + lane * 32;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4 *>(row + ((q ^ (lane & 7)) << 2)) =
+                            make_float4(as * racc[jb + 4 * q], as * racc[jb + 4 * q + 1], as * racc[jb + 4 * q + 2],
+                                        as * racc[jb + 4 * q + 3]);
+                    fence_proxy_async_smem();  // generic writes before the async proxy reads them
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&mapC, tbox_s + (uint32_t)(bi * 4096), n0 + grp * COLS + jb, m0 + sub * 32);
+                        bulk_commit();
+                    }
+                }
+            } else if (V::SPLITK == 1 && epi_ok && V::STAGE_C) {
                 // Coalesced store: the warp's 32 x 32 blocks go through its
                 // staging buffer (row = lane in, four rows of 32 columns per
                 // instruction out), STG_ROWS rows per pass.
@@ -963,6 +1027,9 @@ __global__ void __launch_bounds__(V::THREADS, 1)
                 }
             }
         }
+        // Every box handed to the TMA engine is written before the CTA goes on
+        // (and before its shared memory can be released).
+        if (V::TSTG_BUFS > 0 && args.tma_c && lane == 0) bulk_wait_all();
     }
     __syncthreads();
     if (!epi_ok) s_fail = 1;
